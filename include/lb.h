@@ -1,0 +1,235 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) frontier BFS / SSSP library with the
+ * dynamic load-balancing strategies of "Dynamic Load Balancing Strategies
+ * for Graph Applications on GPUs" (Raval, Nasre, Kumar, R, Vadhiyar,
+ * Pingali; arXiv 1711.00231).
+ *
+ * The problem statement follows the paper's Algorithms "SSSP Pseudocode
+ * illustrating Edge-Based Parallelism" and "... Workload Decomposition":
+ * a directed graph in CSR form (Sec. I and II-B: N + E elements, N + 2E with
+ * weights), dist[] initialised to infinity, dist[source] = 0, and worklist
+ * iterations that relax the out-edges of the active nodes until the worklist
+ * is empty.  BFS is the unit-weight case (Sec. II-B: min level distributes
+ * over level + 1).
+ *
+ * Conventions for every entry point:
+ *  - Status codes only; no exception or signal ever crosses the ABI.  On an
+ *    error, lb_last_error() returns a message for the calling thread.
+ *  - Host pointers are plain host memory; "_dev" pointers are device
+ *    pointers on the graph's device; "stream" is a cudaStream_t (NULL = the
+ *    legacy default stream).
+ *  - All integer arithmetic is exact: levels and distances are identical to
+ *    the plain definitions (fewest hops; least sum of weights) for every
+ *    strategy and every schedule.
+ *  - Calls on one lb_graph are serialised by the library (a per-graph lock
+ *    plus a stream-ordering event); different graphs may be used
+ *    concurrently from different threads.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_graph lb_graph; /* opaque; owns device copies of the CSR */
+
+/* Work distribution strategies.  Baselines (Sec. II) and the paper's three
+ * dynamic strategies (Sec. III). */
+typedef enum lb_strategy {
+    LB_BS = 0,  /* node-based: one thread per worklist node, all its edges
+                   (Sec. II-A; the LonestarGPU-style baseline "BS") */
+    LB_EP = 1,  /* edge-based: one thread per worklist edge of a COO graph;
+                   an updated node's edges are pushed with one reservation
+                   (work chunking, Sec. II-B and IV-D) */
+    LB_WD = 2,  /* workload decomposition: the worklist's edges are cut into
+                   equal contiguous blocks found from the prefix sum of
+                   worklist out-degrees (Sec. III-A) */
+    LB_NS = 3,  /* node splitting: a node of out-degree d > MDT is served as
+                   ceil(d/MDT) nodes of at most MDT edges; MDT from the
+                   degree histogram (Sec. III-B) */
+    LB_HP = 4,  /* hierarchical processing: sub-iterations that relax at most
+                   MDT edges per node, switching to WD below a list-size
+                   threshold (Sec. III-C) */
+    LB_AUTO = 15 /* the library's choice (currently LB_WD) */
+} lb_strategy;
+
+typedef enum lb_status {
+    LB_OK = 0,
+    LB_ERR_ARG = -1,         /* invalid argument or malformed CSR */
+    LB_ERR_OOM = -2,         /* device allocation failed */
+    LB_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    LB_ERR_OVERFLOW = -4,    /* some shortest distance is >= 2^32 - 2 */
+    LB_ERR_TIMEOUT = -5,     /* iteration cap reached (never expected) */
+    LB_ERR_UNSUPPORTED = -6, /* e.g. lb_sssp on a graph created without weights */
+    LB_ERR_INTERNAL = -7     /* a device-side consistency check failed */
+} lb_status;
+
+typedef enum lb_kind { LB_KIND_BFS = 0, LB_KIND_SSSP = 1 } lb_kind;
+
+/* Tunables.  Zero fields take the defaults shown. */
+typedef struct lb_options {
+    int32_t hist_bins;     /* HistogramBinCount of the MDT heuristic (10) */
+    int32_t mdt_override;  /* > 0: use this MDT instead of the histogram (0) */
+    int32_t hp_threshold;  /* HP switches to WD below this list size (1024);
+                              a negative value disables the switch */
+    int32_t loop_mode;     /* 0: device-resident loop (CUDA graph with a
+                              conditional WHILE node); 1: host loop with a
+                              worklist-size readback per iteration, as in the
+                              paper's drivers (0) */
+    int32_t wd_tile;       /* worklist edges per WD tile: 256..8192, a
+                              multiple of 256 (2048) */
+    int32_t ctas_per_sm;   /* CTAs per SM the fixed relax grid is sized for;
+                              0 = the occupancy limit */
+    int32_t reserved[10];
+} lb_options;
+
+/* Device bytes by structure (lb_mem_report).  "extra" is everything a
+ * strategy allocates beyond the CSR arrays, per query workspace. */
+typedef struct lb_mem_stats {
+    int64_t csr_offsets;   /* 8 (n+1) */
+    int64_t csr_cols;      /* 4 m */
+    int64_t csr_weights;   /* 4 m, 0 for an unweighted graph */
+    int64_t status;        /* level / dist working array, 4 n */
+    int64_t visited;       /* BFS visited bitmap + SSSP per-iteration stamps */
+    int64_t node_lists;    /* node worklists (two buffers: id, first edge,
+                              edge prefix) */
+    int64_t tile_starts;   /* WD/HP: first worklist entry of every tile */
+    int64_t coo_src;       /* EP: COO source array (COO dst/wt are the CSR
+                              cols/weights arrays, not duplicated) */
+    int64_t edge_lists;    /* EP: edge worklists (two buffers of m ids) */
+    int64_t sub_lists;     /* HP: sub-worklists (two buffers) */
+    int64_t control;       /* counters, step trace */
+    int64_t extra_total;   /* sum of the fields from status to control */
+    int64_t base_total;    /* csr_offsets + csr_cols + csr_weights */
+    int64_t resident;      /* bytes this graph holds on the device now */
+    int64_t ns_children;   /* NS: child nodes created at the current MDT */
+    int64_t mdt;           /* the MDT NS/HP use (0 if not yet computed) */
+} lb_mem_stats;
+
+/* Per-query counters of the last query on a graph (lb_last_stats). */
+typedef struct lb_query_stats {
+    int64_t iterations;    /* worklist (super-)iterations */
+    int64_t steps;         /* kernel steps (HP sub-iterations counted) */
+    int64_t edges_relaxed; /* edge relaxations executed */
+    int64_t pushes;        /* worklist entries pushed */
+    int64_t mdt;           /* MDT used (NS/HP), else 0 */
+    int32_t status;        /* lb_status of the query */
+    int32_t strategy;      /* strategy that ran */
+    double  device_ms;     /* GPU time of the query (events around it) */
+} lb_query_stats;
+
+/* One kernel step of the last query (lb_last_trace). */
+typedef struct lb_step_record {
+    int32_t level;         /* super-iteration (BFS level of the list) */
+    int32_t mode;          /* 0 relax, 1 HP sub-iteration, 2 HP WD step */
+    int64_t list_size;     /* entries in the list this step consumed */
+    int64_t edges;         /* edges relaxed by this step */
+} lb_step_record;
+
+/* ------------------------------------------------------------ graphs --- */
+
+/* Copies a CSR graph to the device.  offsets: n+1 int64, offsets[0] = 0,
+ * non-decreasing, offsets[n] = m; cols: m int32 in [0, n); weights: m
+ * uint32 or NULL (BFS only).  Requires 1 <= n < 2^31 and m < 2^31.  The
+ * caller keeps ownership of its arrays.  Errors: LB_ERR_ARG (validation),
+ * LB_ERR_OOM, LB_ERR_CUDA. */
+lb_status lb_graph_create(const int64_t *offsets, const int32_t *cols, const uint32_t *weights, int64_t n,
+                          int64_t m, lb_graph **out);
+
+/* Same, from device arrays already on the current device (copied; the
+ * caller keeps ownership).  Only n and the ranges' sizes are checked on the
+ * host; the CSR shape is validated on the device. */
+lb_status lb_graph_create_dev(const int64_t *offsets_dev, const int32_t *cols_dev, const uint32_t *weights_dev,
+                              int64_t n, int64_t m, lb_graph **out);
+
+/* Frees every device allocation of the graph.  NULL is accepted. */
+lb_status lb_graph_destroy(lb_graph *g);
+
+lb_status lb_graph_info(const lb_graph *g, int64_t *n, int64_t *m, int32_t *weighted, int32_t *device);
+
+/* Replaces the graph's options; cached device loops are rebuilt lazily. */
+lb_status lb_set_options(lb_graph *g, const lb_options *o);
+lb_status lb_get_options(const lb_graph *g, lb_options *o);
+
+/* ----------------------------------------------------------- queries --- */
+
+/* BFS from src.  levels_out: host array of n int32 receiving hop counts, -1
+ * for unreachable vertices.  Blocks until the result is on the host. */
+lb_status lb_bfs(lb_graph *g, int32_t src, lb_strategy s, int32_t *levels_out);
+
+/* SSSP from src.  dist_out: host array of n uint32 receiving shortest
+ * distances, 0xFFFFFFFF for unreachable vertices; a distance >= 2^32 - 2 is
+ * written as 0xFFFFFFFE and the call returns LB_ERR_OVERFLOW.  Requires a
+ * weighted graph (LB_ERR_UNSUPPORTED otherwise). */
+lb_status lb_sssp(lb_graph *g, int32_t src, lb_strategy s, uint32_t *dist_out);
+
+/* Device-output forms.  out_dev: n int32 (BFS levels) or n uint32 (SSSP
+ * distances) on the graph's device; parents_dev: NULL or n int32 receiving
+ * a shortest-path tree (parent[src] = src, -1 unreachable; the parent of v
+ * is a u with an edge u->v and dist[u] + w(u,v) = dist[v]).  The call is
+ * asynchronous on `stream`; its status is read with lb_last_stats(). */
+lb_status lb_bfs_dev(lb_graph *g, int32_t src, lb_strategy s, int32_t *out_dev, int32_t *parents_dev, void *stream);
+lb_status lb_sssp_dev(lb_graph *g, int32_t src, lb_strategy s, uint32_t *out_dev, int32_t *parents_dev,
+                      void *stream);
+
+/* Counters and status of the last query on g (waits for it to finish). */
+lb_status lb_last_stats(lb_graph *g, lb_query_stats *out);
+
+/* Per-step schedule of the last query: up to cap records, *len receives the
+ * number of steps recorded (at most 4096 are kept). */
+lb_status lb_last_trace(lb_graph *g, lb_step_record *out, int64_t cap, int64_t *len);
+
+/* ----------------------------------------------------------- memory --- */
+
+/* Device bytes a query with strategy s needs on g, by structure (the
+ * paper's memory axis: Sec. II-B's COO cost 2E / 3E elements vs N + E for
+ * CSR, and Sec. III's per-strategy extra space).  Pure arithmetic on n, m
+ * and the options, except ns_children / mdt, which need the MDT (computed
+ * on the device on first use). */
+lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out);
+
+/* Releases every query workspace of g (the CSR stays). */
+lb_status lb_release_workspaces(lb_graph *g);
+
+/* ------------------------------------------ schedule artefacts --- */
+
+/* Histogram MDT (Sec. III-B, "Automatic Determination of Node Splitting
+ * Threshold") of g's out-degrees, computed on the device: `bins`
+ * equal-width bins over (0, maxDeg], bin k (1-based) holding degrees d with
+ * (k-1) maxDeg < d bins <= k maxDeg; binIndex = tallest bin (smallest on a
+ * tie); MDT = max(1, floor(binIndex maxDeg / bins)); 0 when g has no edges.
+ * bins in [1, 4096].  Any output pointer may be NULL. */
+lb_status lb_mdt(lb_graph *g, int32_t bins, int64_t *mdt, int64_t *max_degree, int32_t *bin_index);
+
+/* Workload-decomposition start offsets (Sec. III-A) for a worklist whose F
+ * nodes have out-degrees deg[] (host), cut over T threads: runs the
+ * library's device worklist-push and tile-start code with
+ * edgesPerThread = ceil(sum(deg) / T).  node_off[t], edge_off[t] (host, T
+ * entries each) receive thread t's first worklist entry and the position of
+ * its first edge inside that entry; threads past the last edge get (F, 0).
+ * *ept receives edgesPerThread.  Uses the current device; F, T <= 2^24. */
+lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_off, int64_t *edge_off,
+                        int64_t *ept);
+
+/* ------------------------------------------------------------- misc --- */
+
+/* Device allocator hook used for every later allocation (NULL, NULL
+ * restores cudaMalloc / cudaFree).  alloc(bytes, ctx) returns a device
+ * pointer or NULL; free(ptr, ctx).  Set it before creating graphs. */
+lb_status lb_set_allocator(void *(*alloc_fn)(size_t, void *), void (*free_fn)(void *, void *), void *ctx);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *lb_last_error(void);
+
+/* Library version string. */
+const char *lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

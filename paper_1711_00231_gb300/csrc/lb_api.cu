@@ -1,0 +1,847 @@
+// Host implementation of the C ABI declared in include/lb.h.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "lb_internal.cuh"
+
+using namespace lbk;
+
+namespace {
+
+thread_local std::string t_err;
+
+std::mutex g_alloc_mu;
+void *(*g_alloc_fn)(size_t, void *) = nullptr;
+void (*g_free_fn)(void *, void *) = nullptr;
+void *g_alloc_ctx = nullptr;
+
+lb_status fail(lb_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+#define LB_CU(call)                                                                                      \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "%s failed: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+    } while (0)
+
+#define LB_TRY(expr)                \
+    do {                            \
+        lb_status s_ = (expr);      \
+        if (s_ != LB_OK) return s_; \
+    } while (0)
+
+struct Allocator {
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+
+    cudaError_t alloc(void **p, size_t bytes) const {
+        if (bytes == 0) bytes = 16;
+        if (alloc_fn) {
+            *p = alloc_fn(bytes, ctx);
+            return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+        }
+        return cudaMalloc(p, bytes);
+    }
+    void release(void *p) const {
+        if (!p) return;
+        if (free_fn) free_fn(p, ctx);
+        else cudaFree(p);
+    }
+};
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int kStrategies = 5;
+
+int64_t round_tiles(int64_t m, int64_t tile) { return m / tile + 2; }
+
+}  // namespace
+
+struct lb_graph {
+    int device = 0;
+    int sms = 0;
+    int64_t n = 0, m = 0;
+    bool weighted = false;
+    bool zero_weight = false;
+    int64_t max_degree = 0;
+    Allocator al;
+    std::mutex mu;
+    lb_options opt{};
+    int64_t resident = 0;
+
+    // CSR
+    int64_t *off = nullptr;
+    int32_t *col = nullptr;
+    uint32_t *w = nullptr;
+
+    // workspace (lazily allocated)
+    Ctl *ctl = nullptr;
+    uint32_t *bitmap = nullptr;
+    uint32_t *epoch = nullptr;
+    uint32_t *out_internal = nullptr;  // result buffer of host-output queries
+    int32_t *par_internal = nullptr;
+    NodeList lists[2]{};
+    NodeList subs[2]{};
+    int64_t list_cap = 0;
+    int64_t tile_cap = 0;
+    bool have_tiles = false;
+    bool have_subs = false;
+    int32_t *elist[2]{};
+    int64_t elist_cap = 0;
+    int32_t *coo_src = nullptr;
+    unsigned long long *scratch = nullptr;  // MDT histogram / counters (4097 words)
+    int64_t *dres = nullptr;                // device results (4 words)
+    int64_t *hres = nullptr;                // pinned host mirror
+    uint32_t *hflag = nullptr;              // pinned host word for the host loop
+
+    int64_t mdt = -1;          // computed with opt.hist_bins (or override)
+    int64_t mdt_bins = -1;
+    int64_t mdt_maxdeg = 0;
+    int32_t mdt_bin = 0;
+    int64_t ns_children = -1;  // at mdt
+
+    cudaGraphExec_t exec[kStrategies][2]{};
+    int grid[kStrategies][2]{};
+
+    cudaStream_t stream = nullptr;  // capture stream and host-output query stream
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
+    int last_strategy = -1;
+
+    template <class T>
+    lb_status alloc(T **p, int64_t count) {
+        void *q = nullptr;
+        const size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+        cudaError_t e = al.alloc(&q, bytes);
+        if (e != cudaSuccess)
+            return fail(LB_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        *p = (T *)q;
+        resident += (int64_t)bytes;
+        return LB_OK;
+    }
+    template <class T>
+    void release(T *&p, int64_t count) {
+        if (!p) return;
+        al.release((void *)p);
+        resident -= (int64_t)((size_t)(count > 0 ? count : 1) * sizeof(T));
+        p = nullptr;
+    }
+};
+
+namespace {
+
+lb_options default_options() {
+    lb_options o;
+    memset(&o, 0, sizeof(o));
+    o.hist_bins = 10;
+    o.mdt_override = 0;
+    o.hp_threshold = 1024;
+    o.loop_mode = 0;
+    o.wd_tile = 2048;
+    o.ctas_per_sm = 0;
+    return o;
+}
+
+lb_status normalise_options(const lb_options *in, lb_options *out) {
+    lb_options d = default_options();
+    lb_options o = *in;
+    if (o.hist_bins == 0) o.hist_bins = d.hist_bins;
+    if (o.hp_threshold == 0) o.hp_threshold = d.hp_threshold;
+    if (o.wd_tile == 0) o.wd_tile = d.wd_tile;
+    if (o.hist_bins < 1 || o.hist_bins > 4096) return fail(LB_ERR_ARG, "hist_bins must be in [1, 4096]");
+    if (o.mdt_override < 0) return fail(LB_ERR_ARG, "mdt_override must be >= 0");
+    if (o.loop_mode != 0 && o.loop_mode != 1) return fail(LB_ERR_ARG, "loop_mode must be 0 or 1");
+    if (o.wd_tile < 256 || o.wd_tile > 8192 || o.wd_tile % 256) return fail(LB_ERR_ARG, "wd_tile must be a multiple of 256 in [256, 8192]");
+    if (o.ctas_per_sm < 0 || o.ctas_per_sm > 32) return fail(LB_ERR_ARG, "ctas_per_sm must be in [0, 32]");
+    *out = o;
+    return LB_OK;
+}
+
+// Waits for the last query so buffers can be freed or reallocated safely.
+void quiesce(lb_graph *g) {
+    if (g->has_last) cudaEventSynchronize(g->ev_done);
+    cudaStreamSynchronize(g->stream);
+}
+
+void drop_execs(lb_graph *g) {
+    for (int s = 0; s < kStrategies; ++s)
+        for (int k = 0; k < 2; ++k)
+            if (g->exec[s][k]) {
+                cudaGraphExecDestroy(g->exec[s][k]);
+                g->exec[s][k] = nullptr;
+            }
+}
+
+void free_lists(lb_graph *g, NodeList *L, int64_t cap, int64_t tcap) {
+    for (int b = 0; b < 2; ++b) {
+        g->release(L[b].v, cap);
+        g->release(L[b].beg, cap);
+        g->release(L[b].scan, cap + 1);
+        g->release(L[b].tstart, tcap);
+    }
+}
+
+lb_status alloc_lists(lb_graph *g, NodeList *L, int64_t cap, int64_t tcap, bool tiles) {
+    for (int b = 0; b < 2; ++b) {
+        LB_TRY(g->alloc(&L[b].v, cap));
+        LB_TRY(g->alloc(&L[b].beg, cap));
+        LB_TRY(g->alloc(&L[b].scan, cap + 1));
+        if (tiles) LB_TRY(g->alloc(&L[b].tstart, tcap));
+    }
+    return LB_OK;
+}
+
+void free_workspace(lb_graph *g) {
+    drop_execs(g);
+    g->release(g->ctl, 1);
+    g->release(g->bitmap, (g->n + 31) / 32);
+    g->release(g->epoch, g->n);
+    g->release(g->out_internal, g->n);
+    g->release(g->par_internal, g->n);
+    free_lists(g, g->lists, g->list_cap, g->tile_cap);
+    free_lists(g, g->subs, g->n, g->tile_cap);
+    g->list_cap = 0;
+    g->have_tiles = false;
+    g->have_subs = false;
+    for (int b = 0; b < 2; ++b) g->release(g->elist[b], g->elist_cap);
+    g->elist_cap = 0;
+    g->release(g->coo_src, g->m);
+}
+
+// MDT with the graph's options (histogram on the device, cached).
+lb_status ensure_mdt(lb_graph *g) {
+    const int64_t bins = g->opt.hist_bins;
+    if (g->opt.mdt_override > 0) {
+        if (g->mdt != g->opt.mdt_override) {
+            g->mdt = g->opt.mdt_override;
+            g->mdt_bins = -1;
+            g->ns_children = -1;
+        }
+    } else if (g->mdt < 0 || g->mdt_bins != bins) {
+        GraphDev gd{g->off, g->col, g->w, g->n, g->m};
+        LB_CU(launch_mdt(gd, (int32_t)bins, g->scratch, g->dres, g->stream));
+        LB_CU(cudaMemcpyAsync(g->hres, g->dres, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+        LB_CU(cudaStreamSynchronize(g->stream));
+        g->mdt = g->hres[0] > 0 ? g->hres[0] : 1;
+        g->mdt_maxdeg = g->hres[1];
+        g->mdt_bin = (int32_t)g->hres[2];
+        g->mdt_bins = bins;
+        g->ns_children = -1;
+    }
+    if (g->ns_children < 0) {
+        GraphDev gd{g->off, g->col, g->w, g->n, g->m};
+        LB_CU(launch_ns_count(gd, (int32_t)g->mdt, g->scratch, g->stream));
+        LB_CU(cudaMemcpyAsync(g->hres, g->scratch, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+        LB_CU(cudaStreamSynchronize(g->stream));
+        g->ns_children = g->hres[0];
+    }
+    return LB_OK;
+}
+
+int64_t node_list_cap(const lb_graph *g, int s) {
+    return s == LB_NS ? g->n + (g->ns_children > 0 ? g->ns_children : 0) : g->n;
+}
+
+// Allocates what strategy s needs; any reallocation invalidates the cached
+// device loops (their kernel parameters hold the pointers).
+lb_status ensure_workspace(lb_graph *g, int s) {
+    if (!g->ctl) {
+        LB_TRY(g->alloc(&g->ctl, 1));
+        LB_CU(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream));
+        LB_TRY(g->alloc(&g->bitmap, (g->n + 31) / 32));
+        LB_TRY(g->alloc(&g->epoch, g->n));
+        LB_CU(cudaMemsetAsync(g->epoch, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
+    }
+    if (s == LB_NS || s == LB_HP) LB_TRY(ensure_mdt(g));
+    if (s == LB_EP) {
+        if (!g->coo_src) {
+            LB_TRY(g->alloc(&g->coo_src, g->m));
+            GraphDev gd{g->off, g->col, g->w, g->n, g->m};
+            LB_CU(launch_coo_build(gd, g->coo_src, g->stream));
+        }
+        if (g->elist_cap < g->m || !g->elist[0]) {
+            quiesce(g);
+            drop_execs(g);
+            for (int b = 0; b < 2; ++b) g->release(g->elist[b], g->elist_cap);
+            g->elist_cap = g->m > 0 ? g->m : 1;
+            for (int b = 0; b < 2; ++b) LB_TRY(g->alloc(&g->elist[b], g->elist_cap));
+        }
+        return LB_OK;
+    }
+    const int64_t cap = node_list_cap(g, s);
+    const bool tiles = (s == LB_WD || s == LB_HP);
+    const int64_t tcap = round_tiles(g->m, g->opt.wd_tile);
+    if (g->list_cap < cap || (tiles && (!g->have_tiles || g->tile_cap != tcap))) {
+        quiesce(g);
+        drop_execs(g);
+        free_lists(g, g->lists, g->list_cap, g->tile_cap);
+        const int64_t newcap = cap > g->list_cap ? cap : g->list_cap;
+        const bool want_tiles = tiles || g->have_tiles;
+        if (g->have_subs) {
+            free_lists(g, g->subs, g->n, g->tile_cap);
+            g->have_subs = false;
+        }
+        g->list_cap = 0;
+        g->have_tiles = false;
+        g->tile_cap = tcap;
+        LB_TRY(alloc_lists(g, g->lists, newcap, tcap, want_tiles));
+        g->list_cap = newcap;
+        g->have_tiles = want_tiles;
+    }
+    if (s == LB_HP && !g->have_subs) {
+        quiesce(g);
+        drop_execs(g);
+        LB_TRY(alloc_lists(g, g->subs, g->n, g->tile_cap, true));
+        g->have_subs = true;
+    }
+    return LB_OK;
+}
+
+StepParams make_params(const lb_graph *g, int s) {
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    p.g = GraphDev{g->off, g->col, g->w, g->n, g->m};
+    p.ctl = g->ctl;
+    for (int b = 0; b < 2; ++b) {
+        p.lists[b] = g->lists[b];
+        p.subs[b] = g->subs[b];
+        p.elist[b] = g->elist[b];
+    }
+    p.coo_src = g->coo_src;
+    p.bitmap = g->bitmap;
+    p.epoch = g->epoch;
+    p.list_cap = s == LB_HP ? (g->list_cap < g->n ? g->list_cap : g->n) : g->list_cap;
+    p.tile_cap = g->tile_cap;
+    p.elist_cap = g->elist_cap;
+    p.tile = g->opt.wd_tile;
+    p.mdt = (int32_t)(g->mdt > 0 ? g->mdt : 1);
+    p.hp_threshold = g->opt.hp_threshold;
+    p.strategy = s;
+    p.use_cond = 0;
+    return p;
+}
+
+int step_grid(lb_graph *g, int s, bool sssp) {
+    int &gr = g->grid[s][sssp ? 1 : 0];
+    if (gr == 0) {
+        int occ = step_blocks_per_sm(s, sssp);
+        if (g->opt.ctas_per_sm > 0 && g->opt.ctas_per_sm < occ) occ = g->opt.ctas_per_sm;
+        gr = occ * g->sms;
+    }
+    return gr;
+}
+
+// Captures one step launch into the body of a conditional WHILE node.
+lb_status build_exec(lb_graph *g, int s, bool sssp, cudaGraphExec_t *out) {
+    cudaGraph_t graph = nullptr;
+    LB_CU(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(LB_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+    }
+    // cudaGraphNodeParams holds a union with a deleted default constructor:
+    // build it in zeroed raw storage.
+    alignas(cudaGraphNodeParams) unsigned char cp_store[sizeof(cudaGraphNodeParams)];
+    memset(cp_store, 0, sizeof(cp_store));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_store);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(LB_ERR_CUDA, "cudaGraphAddNode(conditional): %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    StepParams p = make_params(g, s);
+    p.use_cond = 1;
+    p.cond = h;
+    const int grid = step_grid(g, s, sssp);
+    e = cudaStreamBeginCaptureToGraph(g->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = launch_step(s, sssp, p, grid, g->stream);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(g->stream, &captured);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(LB_ERR_CUDA, "building the device loop failed: %s", cudaGetErrorString(e));
+    return LB_OK;
+}
+
+lb_status status_from_error(uint32_t e) {
+    if (e & (kErrCapacity | kErrShape | kErrBounds))
+        return fail(LB_ERR_INTERNAL, "device consistency check failed (0x%x)", e);
+    if (e & (kErrIterCap | kErrDeadline)) return fail(LB_ERR_TIMEOUT, "iteration cap or time limit reached (0x%x)", e);
+    if (e & kErrOverflow) return fail(LB_ERR_OVERFLOW, "a shortest distance does not fit in 32 bits");
+    return LB_OK;
+}
+
+lb_status run_query(lb_graph *g, int kind, int s, int32_t src, void *out_dev, int32_t *parents_dev,
+                    cudaStream_t st) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    if (src < 0 || (int64_t)src >= g->n) return fail(LB_ERR_ARG, "source %d out of range [0, %lld)", src, (long long)g->n);
+    if (s == LB_AUTO) s = LB_WD;
+    if (s < 0 || s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy %d", s);
+    if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
+    if (!out_dev) return fail(LB_ERR_ARG, "output buffer is NULL");
+    if (parents_dev && kind == LB_KIND_SSSP && g->zero_weight)
+        return fail(LB_ERR_UNSUPPORTED, "parents for graphs with zero-weight edges are not supported");
+    const bool sssp = kind == LB_KIND_SSSP;
+    LB_TRY(ensure_workspace(g, s));
+    if (g->has_last && g->last_stream != st) LB_CU(cudaStreamWaitEvent(st, g->ev_done, 0));
+    // workspace set-up ran on g->stream
+    LB_CU(cudaEventRecord(g->ev_done, g->stream));
+    LB_CU(cudaStreamWaitEvent(st, g->ev_done, 0));
+    StepParams p = make_params(g, s);
+    const uint32_t max_levels = (uint32_t)(g->n + 1 < 0xFFFFFFF0ll ? g->n + 1 : 0xFFFFFFF0ll);
+    const uint64_t max_steps = (uint64_t)1 << 40;
+    const int grid = step_grid(g, s, sssp);
+    LB_CU(cudaEventRecord(g->ev_start, st));
+    const uint64_t time_limit_ns = (uint64_t)120 * 1000000000ull;  // safety net; no query comes close
+    LB_CU(launch_prepare(p, src, (uint32_t *)out_dev, kind, max_levels, max_steps, time_limit_ns, st));
+    LB_CU(launch_init(p, grid, st));
+    if (g->opt.loop_mode == 0) {
+        cudaGraphExec_t &ex = g->exec[s][sssp ? 1 : 0];
+        if (!ex) LB_TRY(build_exec(g, s, sssp, &ex));
+        LB_CU(cudaGraphLaunch(ex, st));
+    } else {
+        for (;;) {
+            LB_CU(launch_step(s, sssp, p, grid, st));
+            LB_CU(cudaMemcpyAsync(g->hflag, &g->ctl->active, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            LB_CU(cudaStreamSynchronize(st));
+            if (!*g->hflag) break;
+        }
+    }
+    LB_CU(launch_finish_query(p, st));
+    if (parents_dev) LB_CU(launch_parents(p, sssp, parents_dev, st));
+    LB_CU(cudaEventRecord(g->ev_stop, st));
+    LB_CU(cudaEventRecord(g->ev_done, st));
+    g->last_stream = st;
+    g->has_last = true;
+    g->last_strategy = s;
+    return LB_OK;
+}
+
+lb_status read_ctl(lb_graph *g, Ctl *h) {
+    LB_CU(cudaEventSynchronize(g->ev_done));
+    LB_CU(cudaMemcpy(h, g->ctl, offsetof(Ctl, trace), cudaMemcpyDeviceToHost));
+    return LB_OK;
+}
+
+lb_status host_query(lb_graph *g, int kind, lb_strategy s, int32_t src, void *host_out) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    if (!host_out) return fail(LB_ERR_ARG, "output buffer is NULL");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    if (!g->out_internal) LB_TRY(g->alloc(&g->out_internal, g->n));
+    LB_TRY(run_query(g, kind, s, src, g->out_internal, nullptr, g->stream));
+    LB_CU(cudaMemcpyAsync(host_out, g->out_internal, sizeof(uint32_t) * (size_t)g->n, cudaMemcpyDeviceToHost,
+                          g->stream));
+    LB_CU(cudaStreamSynchronize(g->stream));
+    Ctl h;
+    LB_TRY(read_ctl(g, &h));
+    return status_from_error(h.error);
+}
+
+lb_status create_common(lb_graph *g) {
+    LB_CU(cudaGetDevice(&g->device));
+    LB_CU(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+    LB_CU(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    LB_CU(cudaEventCreate(&g->ev_start));
+    LB_CU(cudaEventCreate(&g->ev_stop));
+    LB_CU(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
+    LB_CU(cudaMallocHost((void **)&g->hres, 8 * sizeof(int64_t)));
+    LB_CU(cudaMallocHost((void **)&g->hflag, sizeof(uint32_t)));
+    LB_TRY(g->alloc(&g->scratch, 4097));
+    LB_TRY(g->alloc(&g->dres, 4));
+    return LB_OK;
+}
+
+void destroy_graph(lb_graph *g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->has_last) cudaEventSynchronize(g->ev_done);
+    free_workspace(g);
+    g->release(g->scratch, 4097);
+    g->release(g->dres, 4);
+    g->release(g->off, g->n + 1);
+    g->release(g->col, g->m);
+    g->release(g->w, g->m);
+    if (g->hres) cudaFreeHost(g->hres);
+    if (g->hflag) cudaFreeHost(g->hflag);
+    if (g->ev_start) cudaEventDestroy(g->ev_start);
+    if (g->ev_stop) cudaEventDestroy(g->ev_stop);
+    if (g->ev_done) cudaEventDestroy(g->ev_done);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+lb_graph *new_graph(int64_t n, int64_t m, bool weighted) {
+    lb_graph *g = new (std::nothrow) lb_graph();
+    if (!g) return nullptr;
+    g->n = n;
+    g->m = m;
+    g->weighted = weighted;
+    g->opt = default_options();
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g->al.alloc_fn = g_alloc_fn;
+    g->al.free_fn = g_free_fn;
+    g->al.ctx = g_alloc_ctx;
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lb_last_error(void) { return t_err.c_str(); }
+
+const char *lb_version(void) { return "lb 1.0 (sm_103a)"; }
+
+lb_status lb_set_allocator(void *(*alloc_fn)(size_t, void *), void (*free_fn)(void *, void *), void *ctx) {
+    if ((alloc_fn == nullptr) != (free_fn == nullptr)) return fail(LB_ERR_ARG, "give both allocator functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_fn = alloc_fn;
+    g_free_fn = free_fn;
+    g_alloc_ctx = ctx;
+    return LB_OK;
+}
+
+lb_status lb_graph_create(const int64_t *offsets, const int32_t *cols, const uint32_t *weights, int64_t n, int64_t m,
+                          lb_graph **out) {
+    if (!out) return fail(LB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!offsets || (m > 0 && !cols)) return fail(LB_ERR_ARG, "offsets / cols is NULL");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "n must be in [1, 2^31)");
+    if (m < 0 || m >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "m must be in [0, 2^31)");
+    if (offsets[0] != 0) return fail(LB_ERR_ARG, "offsets[0] must be 0");
+    if (offsets[n] != m) return fail(LB_ERR_ARG, "offsets[n] = %lld but m = %lld", (long long)offsets[n], (long long)m);
+    int64_t maxdeg = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        const int64_t d = offsets[u + 1] - offsets[u];
+        if (d < 0) return fail(LB_ERR_ARG, "offsets decrease at %lld", (long long)u);
+        if (d > maxdeg) maxdeg = d;
+    }
+    for (int64_t e = 0; e < m; ++e)
+        if (cols[e] < 0 || (int64_t)cols[e] >= n) return fail(LB_ERR_ARG, "cols[%lld] = %d out of range", (long long)e, cols[e]);
+    bool zero = false;
+    if (weights)
+        for (int64_t e = 0; e < m && !zero; ++e) zero = weights[e] == 0;
+    lb_graph *g = new_graph(n, m, weights != nullptr);
+    if (!g) return fail(LB_ERR_OOM, "host allocation failed");
+    g->zero_weight = zero;
+    g->max_degree = maxdeg;
+    lb_status s = create_common(g);
+    if (s == LB_OK) s = g->alloc(&g->off, n + 1);
+    if (s == LB_OK) s = g->alloc(&g->col, m);
+    if (s == LB_OK && weights) s = g->alloc(&g->w, m);
+    if (s == LB_OK) {
+        cudaError_t e = cudaMemcpy(g->off, offsets, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && m > 0) e = cudaMemcpy(g->col, cols, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && weights && m > 0)
+            e = cudaMemcpy(g->w, weights, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = fail(LB_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
+    }
+    if (s != LB_OK) {
+        destroy_graph(g);
+        return s;
+    }
+    *out = g;
+    return LB_OK;
+}
+
+lb_status lb_graph_create_dev(const int64_t *offsets_dev, const int32_t *cols_dev, const uint32_t *weights_dev,
+                              int64_t n, int64_t m, lb_graph **out) {
+    if (!out) return fail(LB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!offsets_dev || (m > 0 && !cols_dev)) return fail(LB_ERR_ARG, "offsets / cols is NULL");
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "n must be in [1, 2^31)");
+    if (m < 0 || m >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "m must be in [0, 2^31)");
+    lb_graph *g = new_graph(n, m, weights_dev != nullptr);
+    if (!g) return fail(LB_ERR_OOM, "host allocation failed");
+    lb_status s = create_common(g);
+    if (s == LB_OK) s = g->alloc(&g->off, n + 1);
+    if (s == LB_OK) s = g->alloc(&g->col, m);
+    if (s == LB_OK && weights_dev) s = g->alloc(&g->w, m);
+    if (s == LB_OK) {
+        cudaError_t e = cudaMemcpyAsync(g->off, offsets_dev, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToDevice, g->stream);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpyAsync(g->col, cols_dev, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, g->stream);
+        if (e == cudaSuccess && weights_dev && m > 0)
+            e = cudaMemcpyAsync(g->w, weights_dev, sizeof(uint32_t) * (size_t)m, cudaMemcpyDeviceToDevice, g->stream);
+        uint32_t *derr = (uint32_t *)g->dres;
+        if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(uint32_t), g->stream);
+        GraphDev gd{g->off, g->col, g->w, n, m};
+        if (e == cudaSuccess) e = launch_validate(gd, derr, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->hres, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) s = fail(LB_ERR_CUDA, "device graph set-up failed: %s", cudaGetErrorString(e));
+        else if (*(uint32_t *)g->hres & kErrShape) s = fail(LB_ERR_ARG, "malformed CSR (offsets or cols)");
+    }
+    if (s == LB_OK && weights_dev) g->zero_weight = (*(uint32_t *)g->hres & kErrZeroWeight) != 0;
+    if (s != LB_OK) {
+        destroy_graph(g);
+        return s;
+    }
+    *out = g;
+    return LB_OK;
+}
+
+lb_status lb_graph_destroy(lb_graph *g) {
+    destroy_graph(g);
+    return LB_OK;
+}
+
+lb_status lb_graph_info(const lb_graph *g, int64_t *n, int64_t *m, int32_t *weighted, int32_t *device) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (weighted) *weighted = g->weighted ? 1 : 0;
+    if (device) *device = g->device;
+    return LB_OK;
+}
+
+lb_status lb_set_options(lb_graph *g, const lb_options *o) {
+    if (!g || !o) return fail(LB_ERR_ARG, "NULL argument");
+    lb_options n;
+    LB_TRY(normalise_options(o, &n));
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    if (g->has_last) cudaEventSynchronize(g->ev_done);
+    drop_execs(g);
+    memset(g->grid, 0, sizeof(g->grid));
+    if (n.hist_bins != g->opt.hist_bins || n.mdt_override != g->opt.mdt_override) {
+        g->mdt = -1;
+        g->ns_children = -1;
+    }
+    g->opt = n;
+    return LB_OK;
+}
+
+lb_status lb_get_options(const lb_graph *g, lb_options *o) {
+    if (!g || !o) return fail(LB_ERR_ARG, "NULL argument");
+    *o = g->opt;
+    return LB_OK;
+}
+
+lb_status lb_bfs(lb_graph *g, int32_t src, lb_strategy s, int32_t *levels_out) {
+    return host_query(g, LB_KIND_BFS, s, src, levels_out);
+}
+
+lb_status lb_sssp(lb_graph *g, int32_t src, lb_strategy s, uint32_t *dist_out) {
+    return host_query(g, LB_KIND_SSSP, s, src, dist_out);
+}
+
+lb_status lb_bfs_dev(lb_graph *g, int32_t src, lb_strategy s, int32_t *out_dev, int32_t *parents_dev, void *stream) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    return run_query(g, LB_KIND_BFS, s, src, out_dev, parents_dev, (cudaStream_t)stream);
+}
+
+lb_status lb_sssp_dev(lb_graph *g, int32_t src, lb_strategy s, uint32_t *out_dev, int32_t *parents_dev,
+                      void *stream) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    return run_query(g, LB_KIND_SSSP, s, src, out_dev, parents_dev, (cudaStream_t)stream);
+}
+
+lb_status lb_last_stats(lb_graph *g, lb_query_stats *out) {
+    if (!g || !out) return fail(LB_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    memset(out, 0, sizeof(*out));
+    if (!g->has_last) return fail(LB_ERR_ARG, "no query has run on this graph");
+    Ctl h;
+    LB_TRY(read_ctl(g, &h));
+    float ms = 0.f;
+    LB_CU(cudaEventElapsedTime(&ms, g->ev_start, g->ev_stop));
+    out->iterations = h.level;
+    out->steps = (int64_t)h.step;
+    out->edges_relaxed = (int64_t)h.relaxed;
+    out->pushes = (int64_t)h.pushes;
+    out->mdt = (g->last_strategy == LB_NS || g->last_strategy == LB_HP) ? g->mdt : 0;
+    out->strategy = g->last_strategy;
+    out->device_ms = ms;
+    out->status = status_from_error(h.error);
+    return LB_OK;
+}
+
+lb_status lb_last_trace(lb_graph *g, lb_step_record *out, int64_t cap, int64_t *len) {
+    if (!g || !len || (cap > 0 && !out)) return fail(LB_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    if (!g->has_last) return fail(LB_ERR_ARG, "no query has run on this graph");
+    Ctl h;
+    LB_TRY(read_ctl(g, &h));
+    const int64_t k = h.trace_len < (uint32_t)kTraceMax ? h.trace_len : kTraceMax;
+    *len = k;
+    const int64_t c = k < cap ? k : cap;
+    if (c > 0) {
+        static_assert(sizeof(TraceRec) == sizeof(lb_step_record), "trace record layout");
+        LB_CU(cudaMemcpy(out, g->ctl->trace, sizeof(TraceRec) * (size_t)c, cudaMemcpyDeviceToHost));
+    }
+    return LB_OK;
+}
+
+lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
+    if (!g || !out) return fail(LB_ERR_ARG, "NULL argument");
+    if (s == LB_AUTO) s = LB_WD;
+    if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy %d", (int)s);
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    memset(out, 0, sizeof(*out));
+    const int64_t n = g->n, m = g->m;
+    out->csr_offsets = 8 * (n + 1);
+    out->csr_cols = 4 * (m > 0 ? m : 1);
+    out->csr_weights = g->weighted ? 4 * (m > 0 ? m : 1) : 0;
+    out->base_total = out->csr_offsets + out->csr_cols + out->csr_weights;
+    out->status = 4 * n;
+    out->visited = 4 * ((n + 31) / 32) + 4 * n;
+    const int64_t tcap = round_tiles(m, g->opt.wd_tile);
+    if (s == LB_NS || s == LB_HP) {
+        LB_TRY(ensure_mdt(g));
+        out->mdt = g->mdt;
+        out->ns_children = g->ns_children;
+    }
+    if (s == LB_EP) {
+        out->coo_src = 4 * (m > 0 ? m : 1);
+        out->edge_lists = 2 * 4 * (m > 0 ? m : 1);
+    } else {
+        const int64_t cap = node_list_cap(g, s);
+        out->node_lists = 2 * (4 * cap + 8 * cap + 8 * (cap + 1));
+        if (s == LB_WD || s == LB_HP) out->tile_starts = 2 * 4 * tcap;
+        if (s == LB_HP) out->sub_lists = 2 * (4 * n + 8 * n + 8 * (n + 1) + 4 * tcap);
+    }
+    out->control = (int64_t)sizeof(Ctl);
+    out->extra_total = out->status + out->visited + out->node_lists + out->tile_starts + out->coo_src +
+                       out->edge_lists + out->sub_lists + out->control;
+    out->resident = g->resident;
+    return LB_OK;
+}
+
+lb_status lb_release_workspaces(lb_graph *g) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    if (g->has_last) cudaEventSynchronize(g->ev_done);
+    cudaStreamSynchronize(g->stream);
+    free_workspace(g);
+    g->has_last = false;
+    return LB_OK;
+}
+
+lb_status lb_mdt(lb_graph *g, int32_t bins, int64_t *mdt, int64_t *max_degree, int32_t *bin_index) {
+    if (!g) return fail(LB_ERR_ARG, "graph is NULL");
+    if (bins < 1 || bins > 4096) return fail(LB_ERR_ARG, "bins must be in [1, 4096]");
+    std::lock_guard<std::mutex> lk(g->mu);
+    DeviceGuard dg(g->device);
+    if (g->has_last) LB_CU(cudaStreamWaitEvent(g->stream, g->ev_done, 0));
+    GraphDev gd{g->off, g->col, g->w, g->n, g->m};
+    LB_CU(launch_mdt(gd, bins, g->scratch, g->dres, g->stream));
+    LB_CU(cudaMemcpyAsync(g->hres, g->dres, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+    LB_CU(cudaStreamSynchronize(g->stream));
+    if (mdt) *mdt = g->hres[0];
+    if (max_degree) *max_degree = g->hres[1];
+    if (bin_index) *bin_index = (int32_t)g->hres[2];
+    return LB_OK;
+}
+
+lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_off, int64_t *edge_off,
+                        int64_t *ept) {
+    if (F < 0 || F > ((int64_t)1 << 24) || T < 1 || T > ((int64_t)1 << 24)) return fail(LB_ERR_ARG, "F or T out of range");
+    if ((F > 0 && !deg) || !node_off || !edge_off || !ept) return fail(LB_ERR_ARG, "NULL argument");
+    int64_t E = 0;
+    for (int64_t i = 0; i < F; ++i) {
+        if (deg[i] < 0 || deg[i] >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "deg[%lld] out of range", (long long)i);
+        E += deg[i];
+    }
+    if (E >= ((int64_t)1 << 31)) return fail(LB_ERR_ARG, "sum of degrees must be < 2^31");
+    Allocator al;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        al.alloc_fn = g_alloc_fn;
+        al.free_fn = g_free_fn;
+        al.ctx = g_alloc_ctx;
+    }
+    cudaStream_t st = nullptr;
+    LB_CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    void *bufs[7] = {nullptr};
+    const size_t sizes[7] = {sizeof(int64_t) * (size_t)(F > 0 ? F : 1), sizeof(int32_t) * (size_t)(F > 0 ? F : 1),
+                             sizeof(int64_t) * (size_t)(F > 0 ? F : 1), sizeof(int64_t) * (size_t)(F + 1),
+                             sizeof(int32_t) * (size_t)(T + 1), sizeof(Ctl), sizeof(int64_t)};
+    lb_status status = LB_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = al.alloc(&bufs[i], sizes[i]);
+    std::string msg;
+    if (e == cudaSuccess && F > 0) e = cudaMemcpyAsync(bufs[0], deg, sizes[0], cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bufs[5], 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bufs[4], 0, sizes[4], st);
+    NodeList L{(int32_t *)bufs[1], (int64_t *)bufs[2], (int64_t *)bufs[3], (int32_t *)bufs[4]};
+    if (e == cudaSuccess) e = launch_wd_offsets((const int64_t *)bufs[0], F, T, L, (Ctl *)bufs[5], (int64_t *)bufs[6], st);
+    int64_t h_ept = 0;
+    int32_t *h_ts = new (std::nothrow) int32_t[(size_t)T + 1];
+    int64_t *h_scan = new (std::nothrow) int64_t[(size_t)F + 1];
+    if (!h_ts || !h_scan) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_ept, bufs[6], sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_ts, bufs[4], sizes[4], cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_scan, bufs[3], sizes[3], cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        status = fail(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "lb_wd_offsets: %s", cudaGetErrorString(e));
+    } else {
+        *ept = h_ept;
+        for (int64_t t = 0; t < T; ++t) {
+            const int64_t s0 = t * h_ept;
+            if (h_ept == 0 || s0 >= E) {
+                node_off[t] = F;
+                edge_off[t] = 0;
+            } else {
+                node_off[t] = h_ts[t];
+                edge_off[t] = s0 - h_scan[h_ts[t]];
+            }
+        }
+    }
+    delete[] h_ts;
+    delete[] h_scan;
+    for (int i = 0; i < 7; ++i)
+        if (bufs[i]) al.release(bufs[i]);
+    cudaStreamDestroy(st);
+    return status;
+}
+
+}  // extern "C"

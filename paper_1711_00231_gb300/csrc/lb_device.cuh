@@ -1,0 +1,266 @@
+// Device building blocks shared by the step kernels of every strategy.
+//
+//  * Relax ops (the paper's Algorithms for EP and WD: "altdist =
+//    dist[src] + weight; if dist[dst] > altdist: update dist, push dst"):
+//      BFS  - claim v with atomicOr on a visited bitmap, level[v] = L + 1;
+//      SSSP - atomicMin on dist[v]; queue v only for the first improvement
+//             in an iteration (stamp exchange), so a list never exceeds n.
+//    Both run test-then-atomic: the plain read can only be stale in the
+//    direction that costs an extra atomic, never one that loses an update.
+//  * Warp push buffers: the paper pushes with one atomic per node ("work
+//    chunking", Sec. II-B / IV-D).  Here a warp collects up to kWB pushed
+//    nodes in shared memory and reserves their list slots and their edges
+//    with ONE 64-bit atomicAdd on a packed (entries << 32 | edges) counter.
+//    The reservation returns consistent bases for both, so each entry's
+//    edge prefix (the WD prefix sum of Sec. III-A, Thrust's inclusive scan
+//    in the paper) and the WD tile starts (the paper's find_offsets) come
+//    out of the push itself: no scan or offset kernel runs per iteration.
+//  * The last CTA of every step kernel finalises the iteration (swaps the
+//    lists, records the trace, sets the CUDA-graph loop condition), so each
+//    iteration is a single kernel launch.
+#pragma once
+
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+constexpr int kWB = 128;  // entries per warp push buffer (multiple of 32)
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// what a flush writes
+enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2 };
+
+struct WarpBuf {
+    int64_t beg[kWB];
+    int32_t v[kWB];
+    uint32_t deg[kWB];
+};
+
+struct WarpScratch {
+    uint32_t pu[kWB];  // exclusive prefix of output units
+    uint32_t pe[kWB];  // exclusive prefix of edges
+};
+
+struct FlushOut {
+    NodeList list;     // node / granule output
+    int32_t *elist;    // edge-id output
+    unsigned long long *pack;
+    int64_t cap;       // entries the output can hold
+    int64_t tile_cap;  // tstart entries
+    int32_t tile;
+    int32_t mdt;
+};
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+template <int KIND>
+__device__ __forceinline__ uint32_t out_units(uint32_t deg, int32_t mdt) {
+    if (KIND == kOutEdges) return deg;
+    if (KIND == kOutGranule) return deg <= (uint32_t)mdt ? 1u : (deg + (uint32_t)mdt - 1u) / (uint32_t)mdt;
+    return 1u;
+}
+
+// Warp-uniform: every lane of the warp calls it with the same cnt.
+// Requires cnt + 32 <= kWB on entry.
+__device__ __forceinline__ void wpush(WarpBuf &b, uint32_t &cnt, bool want, int32_t v, int64_t beg, uint32_t deg) {
+    const unsigned m = __ballot_sync(kFull, want);
+    if (want) {
+        const uint32_t s = cnt + __popc(m & lanemask_lt());
+        b.v[s] = v;
+        b.beg[s] = beg;
+        b.deg[s] = deg;
+    }
+    cnt += __popc(m);
+    __syncwarp();
+}
+
+// largest i in [0, n) with a[i] <= x (a[0] <= x assumed)
+__device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, uint32_t x) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Warp-uniform flush of a warp push buffer into a global list.
+template <int KIND, bool TILED>
+__device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o, Ctl *ctl) {
+    if (cnt == 0) return;
+    const uint32_t lane = lane_id();
+    uint32_t run_u = 0, run_e = 0;
+    for (uint32_t c = 0; c < cnt; c += 32) {
+        const uint32_t i = c + lane;
+        const uint32_t d = i < cnt ? b.deg[i] : 0u;
+        const uint32_t u = i < cnt ? out_units<KIND>(d, o.mdt) : 0u;
+        uint32_t iu = u, ie = d;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const uint32_t tu = __shfl_up_sync(kFull, iu, k);
+            const uint32_t te = __shfl_up_sync(kFull, ie, k);
+            if ((int)lane >= k) { iu += tu; ie += te; }
+        }
+        if (i < cnt) { s.pu[i] = run_u + iu - u; s.pe[i] = run_e + ie - d; }
+        run_u += __shfl_sync(kFull, iu, 31);
+        run_e += __shfl_sync(kFull, ie, 31);
+    }
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(o.pack, ((unsigned long long)run_u << 32) | (unsigned long long)run_e);
+    old = __shfl_sync(kFull, old, 0);
+    __syncwarp();
+    const int64_t ubase = (int64_t)(old >> 32);
+    const int64_t ebase = (int64_t)(old & 0xFFFFFFFFull);
+    if (ubase + (int64_t)run_u > o.cap) {
+        if (lane == 0) atomicOr(&ctl->error, kErrCapacity);
+        cnt = 0;
+        __syncwarp();
+        return;
+    }
+    if (KIND == kOutNode) {
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            const int64_t pos = ubase + i;
+            const int64_t S = ebase + s.pe[i];
+            o.list.v[pos] = b.v[i];
+            o.list.beg[pos] = b.beg[i];
+            o.list.scan[pos] = S;
+            if (TILED) {
+                const int64_t E = S + b.deg[i];
+                for (int64_t k = (S + o.tile - 1) / o.tile; k * o.tile < E; ++k)
+                    if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+            }
+        }
+    } else {
+        for (uint32_t j = lane; j < run_u; j += 32) {
+            const uint32_t i = smem_upper(s.pu, cnt, j);
+            const int64_t k = (int64_t)(j - s.pu[i]);
+            if (KIND == kOutGranule) {
+                const int64_t pos = ubase + j;
+                o.list.v[pos] = b.v[i];
+                o.list.beg[pos] = b.beg[i] + k * o.mdt;
+                o.list.scan[pos] = ebase + s.pe[i] + k * o.mdt;
+            } else {
+                o.elist[ubase + j] = (int32_t)(b.beg[i] + k);
+            }
+        }
+    }
+    if (lane == 0) atomicAdd(&ctl->pushes, (unsigned long long)run_u);
+    cnt = 0;
+    __syncwarp();
+}
+
+// ---- relax ops ------------------------------------------------------------
+
+// BFS: true iff this thread discovered v (and set its level).
+__device__ __forceinline__ bool bfs_claim(uint32_t *__restrict__ bitmap, uint32_t *__restrict__ status, int32_t v,
+                                          uint32_t newlev) {
+    const uint32_t word = (uint32_t)v >> 5, bit = 1u << ((uint32_t)v & 31u);
+    if (bitmap[word] & bit) return false;
+    if (atomicOr(&bitmap[word], bit) & bit) return false;
+    status[v] = newlev;
+    return true;
+}
+
+// SSSP: true iff v improved and this is v's first queueing this iteration.
+__device__ __forceinline__ bool sssp_relax(uint32_t *__restrict__ status, uint32_t *__restrict__ epoch, int32_t v,
+                                           uint32_t du, uint32_t w, uint32_t stamp, Ctl *ctl) {
+    if (du == kInf) return false;
+    const uint64_t a64 = (uint64_t)du + (uint64_t)w;
+    const uint32_t alt = a64 >= kSat ? kSat : (uint32_t)a64;
+    if (alt >= status[v]) return false;
+    const uint32_t old = atomicMin(&status[v], alt);
+    if (alt >= old) return false;
+    if (alt == kSat) atomicOr(&ctl->error, kErrSaturated);
+    if (epoch[v] == stamp) return false;
+    return atomicExch(&epoch[v], stamp) != stamp;
+}
+
+// ---- end-of-step protocol ----------------------------------------------------
+
+__device__ __forceinline__ bool block_is_last(Ctl *ctl) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
+        s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ void trace_append(Ctl *ctl, int32_t mode, int64_t list_size, int64_t edges) {
+    const uint32_t t = ctl->trace_len;
+    if (t < (uint32_t)kTraceMax) {
+        ctl->trace[t].level = (int32_t)ctl->level;
+        ctl->trace[t].mode = mode;
+        ctl->trace[t].list_size = list_size;
+        ctl->trace[t].edges = edges;
+        ctl->trace_len = t + 1;
+    }
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_loop(const StepParams &p, Ctl *ctl, bool more) {
+    if (ctl->level >= ctl->max_levels || ctl->step >= ctl->max_steps) {
+        if (more) ctl->error |= kErrIterCap;
+        more = false;
+    }
+    if (more && global_ns() > ctl->t_deadline) {
+        ctl->error |= kErrDeadline;
+        more = false;
+    }
+    ctl->active = more ? 1u : 0u;
+    if (!more) ctl->epoch_next = ctl->epoch_base + ctl->level + 1;
+    if (p.use_cond) cudaGraphSetConditional(p.cond, more ? 1u : 0u);
+}
+
+// Finalise a plain (non-HP) step: the output list becomes the input list.
+// node_list: the output is a node / granule list needing a scan sentinel.
+__device__ __forceinline__ void finish_plain_step(const StepParams &p, Ctl *ctl, bool node_list, int64_t cap) {
+    __threadfence();
+    const unsigned long long pk = ld_volatile(&ctl->out_pack);
+    int64_t cnt = (int64_t)(pk >> 32);
+    const int64_t edges = (int64_t)(pk & 0xFFFFFFFFull);
+    if (cnt > cap) { ctl->error |= kErrCapacity; cnt = cap; }
+    const int64_t step_edges = node_list ? (int64_t)ctl->in_edges : (int64_t)ctl->in_cnt;
+    trace_append(ctl, kModeRelax, ctl->in_cnt, step_edges);
+    ctl->relaxed += (unsigned long long)step_edges;
+    const uint32_t out = ctl->par ^ 1u;
+    if (node_list) p.lists[out].scan[cnt] = edges;
+    ctl->par = out;
+    ctl->in_cnt = (uint32_t)cnt;
+    ctl->in_edges = (uint64_t)edges;
+    ctl->out_pack = 0ull;
+    ctl->level += 1;
+    ctl->step += 1;
+    ctl->blocks_done = 0;
+    set_loop(p, ctl, cnt > 0);
+    __threadfence();
+}
+
+// Largest k in [lo, hi) with scan[k] <= e (read-only list, L1-cached).
+__device__ __forceinline__ int64_t list_search(const int64_t *__restrict__ scan, int64_t lo, int64_t hi, int64_t e) {
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(scan + mid) <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace lbk

@@ -1,0 +1,138 @@
+// Internal types shared by the host API and the device kernels of liblb.
+//
+// Data layout in HBM (one query workspace per graph, reused by every query):
+//   status[n]        uint32 level / distance, 0xFFFFFFFF = not reached
+//   bitmap[n/32]     BFS visited bits (claimed with atomicOr)
+//   epoch[n]         SSSP stamp of the iteration that last queued a vertex
+//   node lists x2    worklist entries {v int32, beg int64, scan int64} plus
+//                    tstart[] (first entry of every WD tile); double-buffered
+//   sub lists x2     HP sub-worklists, same layout
+//   edge lists x2    EP worklists of CSR edge ids (COO edge index = CSR index)
+//   coo_src[m]       EP: source of every CSR edge
+//   Ctl              loop state, counters and the step trace
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lb.h"
+
+namespace lbk {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;  // not reached
+constexpr uint32_t kSat = 0xFFFFFFFEu;  // saturated distance (>= 2^32 - 2)
+constexpr int kBlock = 256;             // threads per CTA of every step kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kTraceMax = 4096;
+
+// error bits in Ctl::error
+enum : uint32_t {
+    kErrCapacity = 1u,   // a push would exceed a list's capacity (dropped)
+    kErrIterCap = 2u,    // iteration / step cap reached
+    kErrSaturated = 4u,  // some relaxation saturated at 2^32 - 2
+    kErrShape = 8u,      // CSR validation failed (device-created graphs)
+    kErrOverflow = 16u,  // a final distance is saturated (>= 2^32 - 2)
+    kErrZeroWeight = 32u,  // validation: the graph has a zero-weight edge (not an error)
+    kErrBounds = 64u,    // a list entry pointed outside the graph (access skipped)
+    kErrDeadline = 128u, // the query exceeded its device-side time limit
+};
+
+// step modes recorded in the trace
+enum : int32_t { kModeRelax = 0, kModeHpSub = 1, kModeHpWd = 2 };
+
+// which list an HP step reads
+enum : uint32_t { kHpFromSuper = 0, kHpFromSub = 1 };
+
+struct TraceRec {
+    int32_t level;
+    int32_t mode;
+    int64_t list_size;
+    int64_t edges;
+};
+
+struct Ctl {
+    // query parameters (written by the prepare kernel)
+    uint32_t *status;
+    int32_t src;
+    int32_t kind;  // 0 BFS, 1 SSSP
+    // loop state
+    uint32_t level;     // super-iteration index = BFS level of the input list
+    uint32_t par;       // input node list = lists[par], output = lists[par ^ 1]
+    uint32_t in_cnt;    // entries of the input list
+    uint32_t hp_from;   // HP: input list is the super list or a sub list
+    uint64_t in_edges;  // edges of the input list (sum of entry lengths)
+    unsigned long long out_pack;  // output list: (entries << 32) | edges
+    unsigned long long sub_pack;  // HP sub-list output: (entries << 32) | edges
+    uint32_t hp_kind;   // HP: next step is a sub-iteration (1) or WD (2)
+    uint32_t hp_sub;    // HP: sub-iteration index inside the super-iteration
+    uint32_t sub_in;    // HP: sub list buffer read when hp_from == kHpFromSub
+    uint32_t blocks_done;
+    uint32_t active;    // loop condition
+    uint32_t error;
+    uint32_t epoch_base;    // SSSP: iteration i stamps epoch_base + i
+    uint32_t epoch_next;    // first stamp free for the next query
+    uint32_t epoch_reset;   // init kernel must clear the stamp array
+    uint32_t max_levels;
+    uint64_t max_steps;
+    uint64_t step;
+    uint64_t t_deadline;  // %globaltimer (ns) after which the loop stops
+    unsigned long long relaxed;
+    unsigned long long pushes;
+    uint32_t trace_len;
+    uint32_t pad;
+    TraceRec trace[kTraceMax];
+};
+
+struct GraphDev {
+    const int64_t *off;
+    const int32_t *col;
+    const uint32_t *w;
+    int64_t n;
+    int64_t m;
+};
+
+struct NodeList {
+    int32_t *v;
+    int64_t *beg;
+    int64_t *scan;    // exclusive prefix of entry lengths; scan[cnt] = total
+    int32_t *tstart;  // tstart[k]: entry holding list edge k * tile
+};
+
+struct StepParams {
+    GraphDev g;
+    Ctl *ctl;
+    NodeList lists[2];
+    NodeList subs[2];
+    int32_t *elist[2];
+    const int32_t *coo_src;
+    uint32_t *bitmap;
+    uint32_t *epoch;
+    int64_t list_cap;
+    int64_t tile_cap;
+    int64_t elist_cap;
+    int32_t tile;
+    int32_t mdt;
+    int32_t hp_threshold;  // <= 0: never switch to WD
+    int32_t strategy;
+    int32_t use_cond;
+    int32_t pad;
+    cudaGraphConditionalHandle cond;
+};
+
+// ---- launch entry points implemented by the strategy translation units --
+cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, cudaStream_t st);
+int step_blocks_per_sm(int strategy, bool sssp);
+cudaError_t launch_prepare(const StepParams &p, int32_t src, uint32_t *status, int kind, uint32_t max_levels,
+                           uint64_t max_steps, uint64_t time_limit_ns, cudaStream_t st);
+cudaError_t launch_init(const StepParams &p, int grid, cudaStream_t st);
+cudaError_t launch_finish_query(const StepParams &p, cudaStream_t st);
+cudaError_t launch_coo_build(const GraphDev &g, int32_t *coo_src, cudaStream_t st);
+cudaError_t launch_mdt(const GraphDev &g, int32_t bins, unsigned long long *scratch, int64_t *result,
+                       cudaStream_t st);
+cudaError_t launch_validate(const GraphDev &g, uint32_t *err, cudaStream_t st);
+cudaError_t launch_ns_count(const GraphDev &g, int32_t mdt, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList list, Ctl *ctl, int64_t *ept_out,
+                              cudaStream_t st);
+cudaError_t launch_parents(const StepParams &p, bool sssp, int32_t *parents, cudaStream_t st);
+
+}  // namespace lbk

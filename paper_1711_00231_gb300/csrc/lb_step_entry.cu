@@ -1,0 +1,30 @@
+// BS (node per thread) and NS (granule per thread) step kernels.
+#include "lb_launch.h"
+#include "lb_steps.cuh"
+
+namespace lbk {
+
+template <bool S, int K>
+static int occ() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_entry<S, K>, kBlock, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_step_entry(bool sssp, bool granules, const StepParams &p, int grid, cudaStream_t st) {
+    if (sssp) {
+        if (granules) k_step_entry<true, kOutGranule><<<grid, kBlock, 0, st>>>(p);
+        else k_step_entry<true, kOutNode><<<grid, kBlock, 0, st>>>(p);
+    } else {
+        if (granules) k_step_entry<false, kOutGranule><<<grid, kBlock, 0, st>>>(p);
+        else k_step_entry<false, kOutNode><<<grid, kBlock, 0, st>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+int occupancy_step_entry(bool sssp, bool granules) {
+    if (sssp) return granules ? occ<true, kOutGranule>() : occ<true, kOutNode>();
+    return granules ? occ<false, kOutGranule>() : occ<false, kOutNode>();
+}
+
+}  // namespace lbk

@@ -1,0 +1,393 @@
+// Step kernels: one launch = one worklist iteration (or one HP sub-step).
+//
+// Every kernel runs on a fixed, persistent-style grid (a multiple of the SM
+// count) and reads the sizes of its input list from the device control
+// block, so the same launch can be captured once into a CUDA graph and
+// replayed by a conditional WHILE node until the worklist is empty.
+#pragma once
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+// ---------------------------------------------------------------------------
+// Thread per worklist entry: BS (entries are whole nodes) and NS (entries
+// are granules of at most MDT edges).  The edge loop is warp-uniform so the
+// warp can push between edges; lanes whose entry is exhausted idle, which is
+// exactly the load imbalance the node-based baseline exhibits (Sec. II-A).
+// ---------------------------------------------------------------------------
+template <bool SSSP, int OUTK>
+__global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const uint32_t par = ctl->par;
+    const int64_t in_cnt = ctl->in_cnt;
+    const uint32_t level = ctl->level;
+    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *status = ctl->status;
+    const NodeList in = p.lists[par];
+    FlushOut o;
+    o.list = p.lists[par ^ 1u];
+    o.elist = nullptr;
+    o.pack = &ctl->out_pack;
+    o.cap = p.list_cap;
+    o.tile_cap = p.tile_cap;
+    o.tile = p.tile;
+    o.mdt = p.mdt;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    WarpBuf &wb = s_wb[warp];
+    WarpScratch &ws = s_ws[warp];
+    uint32_t cnt = 0;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
+        const int64_t i = base + lane;
+        int64_t cur = 0, end = 0;
+        uint32_t du = 0;
+        if (i < in_cnt) {
+            cur = __ldg(in.beg + i);
+            end = cur + (__ldg(in.scan + i + 1) - __ldg(in.scan + i));
+            if (cur < 0 || end > p.g.m || cur > end) {
+                atomicOr(&ctl->error, kErrBounds);
+                cur = end = 0;
+            } else if (SSSP) {
+                du = status[__ldg(in.v + i)];
+            }
+        }
+        while (__any_sync(kFull, cur < end)) {
+            bool want = false;
+            int32_t v = 0;
+            int64_t vb = 0;
+            uint32_t vd = 0;
+            if (cur < end) {
+                v = __ldg(p.g.col + cur);
+                const bool hit = SSSP ? sssp_relax(status, p.epoch, v, du, __ldg(p.g.w + cur), stamp, ctl)
+                                      : bfs_claim(p.bitmap, status, v, level + 1);
+                if (hit) {
+                    vb = __ldg(p.g.off + v);
+                    vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
+                    want = vd > 0;
+                }
+                ++cur;
+            }
+            wpush(wb, cnt, want, v, vb, vd);
+            if (cnt > kWB - 32) wflush<OUTK, false>(wb, ws, cnt, o, ctl);
+        }
+    }
+    wflush<OUTK, false>(wb, ws, cnt, o, ctl);
+    if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
+}
+
+// ---------------------------------------------------------------------------
+// Workload decomposition over CTA tiles.  The input list's edges (in list
+// order) are cut into tiles of p.tile edges; tile t starts in entry
+// tstart[t] (written by the push that created the list).  Inside a tile,
+// consecutive threads take consecutive edges, so a node's adjacency is read
+// coalesced, and a thread finds the entry of each of its edges by a short
+// binary search over the tile's slice of the edge prefix.
+// ---------------------------------------------------------------------------
+template <bool SSSP, int ITEMS>
+__device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt,
+                                         int64_t E, WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
+                                         uint32_t *status, uint32_t level, uint32_t stamp) {
+    const int64_t T = p.tile;
+    const int64_t ntiles = (E + T - 1) / T;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t e0 = t * T;
+        const int64_t e1 = min(e0 + T, E);
+        int64_t i0 = __ldg(in.tstart + t);
+        int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldg(in.tstart + t + 1) + 1, in_cnt) : in_cnt;
+        if (i0 < 0 || i0 >= ihi) {  // inconsistent tile start: flag, fall back to the whole list
+            if (threadIdx.x == 0) atomicOr(&ctl->error, kErrBounds);
+            i0 = 0;
+            ihi = in_cnt;
+        }
+        for (int64_t r0 = e0; r0 < e1; r0 += (int64_t)kBlock * ITEMS) {
+            int32_t vv[ITEMS];
+            uint32_t ww[ITEMS], dd[ITEMS];
+            bool ok[ITEMS];
+#pragma unroll
+            for (int it = 0; it < ITEMS; ++it) {
+                const int64_t e = r0 + (int64_t)it * kBlock + threadIdx.x;
+                ok[it] = e < e1;
+                vv[it] = 0;
+                ww[it] = 0;
+                dd[it] = 0;
+                if (ok[it]) {
+                    const int64_t k = list_search(in.scan, i0, ihi, e);
+                    const int64_t eidx = __ldg(in.beg + k) + (e - __ldg(in.scan + k));
+                    if ((uint64_t)eidx >= (uint64_t)p.g.m) {
+                        atomicOr(&ctl->error, kErrBounds);
+                        ok[it] = false;
+                    } else {
+                        vv[it] = __ldg(p.g.col + eidx);
+                        if (SSSP) {
+                            ww[it] = __ldg(p.g.w + eidx);
+                            dd[it] = status[__ldg(in.v + k)];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < ITEMS; ++it) {
+                bool want = false;
+                int64_t vb = 0;
+                uint32_t vd = 0;
+                if (ok[it]) {
+                    const bool hit = SSSP ? sssp_relax(status, p.epoch, vv[it], dd[it], ww[it], stamp, ctl)
+                                          : bfs_claim(p.bitmap, status, vv[it], level + 1);
+                    if (hit) {
+                        vb = __ldg(p.g.off + vv[it]);
+                        vd = (uint32_t)(__ldg(p.g.off + vv[it] + 1) - vb);
+                        want = vd > 0;
+                    }
+                }
+                wpush(wb, cnt, want, vv[it], vb, vd);
+                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o, ctl);
+            }
+        }
+    }
+}
+
+template <bool SSSP, int ITEMS>
+__global__ void __launch_bounds__(kBlock) k_step_wd(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const uint32_t par = ctl->par;
+    const int64_t in_cnt = ctl->in_cnt;
+    const int64_t E = (int64_t)ctl->in_edges;
+    const uint32_t level = ctl->level;
+    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *status = ctl->status;
+    const NodeList in = p.lists[par];
+    FlushOut o;
+    o.list = p.lists[par ^ 1u];
+    o.elist = nullptr;
+    o.pack = &ctl->out_pack;
+    o.cap = p.list_cap;
+    o.tile_cap = p.tile_cap;
+    o.tile = p.tile;
+    o.mdt = p.mdt;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t cnt = 0;
+    wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
+    wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o, ctl);
+    if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
+}
+
+// ---------------------------------------------------------------------------
+// Edge-based distribution (Sec. II-B): one thread per worklist edge of the
+// COO graph (source from coo_src, destination and weight from the CSR
+// arrays, which double as the COO dst / wt arrays).  An updated node pushes
+// all of its edge ids with one reservation (work chunking).
+// ---------------------------------------------------------------------------
+template <bool SSSP, int ITEMS>
+__global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const uint32_t par = ctl->par;
+    const int64_t in_cnt = ctl->in_cnt;
+    const uint32_t level = ctl->level;
+    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *status = ctl->status;
+    const int32_t *in = p.elist[par];
+    FlushOut o;
+    o.list = p.lists[0];
+    o.elist = p.elist[par ^ 1u];
+    o.pack = &ctl->out_pack;
+    o.cap = p.elist_cap;
+    o.tile_cap = 0;
+    o.tile = p.tile;
+    o.mdt = p.mdt;
+    const uint32_t warp = threadIdx.x >> 5;
+    WarpBuf &wb = s_wb[warp];
+    WarpScratch &ws = s_ws[warp];
+    uint32_t cnt = 0;
+    const int64_t chunk = (int64_t)kBlock * ITEMS;
+    for (int64_t r0 = (int64_t)blockIdx.x * chunk; r0 < in_cnt; r0 += (int64_t)gridDim.x * chunk) {
+        int32_t vv[ITEMS];
+        uint32_t ww[ITEMS], dd[ITEMS];
+        bool ok[ITEMS];
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const int64_t i = r0 + (int64_t)it * kBlock + threadIdx.x;
+            ok[it] = i < in_cnt;
+            vv[it] = 0;
+            ww[it] = 0;
+            dd[it] = 0;
+            if (ok[it]) {
+                const int32_t e = __ldg(in + i);
+                if (e < 0 || (int64_t)e >= p.g.m) {
+                    atomicOr(&ctl->error, kErrBounds);
+                    ok[it] = false;
+                    continue;
+                }
+                vv[it] = __ldg(p.g.col + e);
+                if (SSSP) {
+                    ww[it] = __ldg(p.g.w + e);
+                    dd[it] = status[__ldg(p.coo_src + e)];
+                }
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            bool want = false;
+            int64_t vb = 0;
+            uint32_t vd = 0;
+            if (ok[it]) {
+                const bool hit = SSSP ? sssp_relax(status, p.epoch, vv[it], dd[it], ww[it], stamp, ctl)
+                                      : bfs_claim(p.bitmap, status, vv[it], level + 1);
+                if (hit) {
+                    vb = __ldg(p.g.off + vv[it]);
+                    vd = (uint32_t)(__ldg(p.g.off + vv[it] + 1) - vb);
+                    want = vd > 0;
+                }
+            }
+            wpush(wb, cnt, want, vv[it], vb, vd);
+            if (cnt > kWB - 32) wflush<kOutEdges, false>(wb, ws, cnt, o, ctl);
+        }
+    }
+    wflush<kOutEdges, false>(wb, ws, cnt, o, ctl);
+    if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, false, p.elist_cap);
+}
+
+// ---------------------------------------------------------------------------
+// Hierarchical processing (Sec. III-C).  One launch is one step of the
+// super-iteration: either a sub-iteration over the current list (each entry
+// relaxes at most MDT edges; entries with edges left are pushed, with their
+// remaining range, to the next sub-list) or, when the list is shorter than
+// the threshold, one workload-decomposition step over everything left.
+// Nodes updated in any step go to the next super worklist.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
+    __threadfence();
+    const unsigned long long pk = ld_volatile(&ctl->out_pack);
+    const unsigned long long spk = ld_volatile(&ctl->sub_pack);
+    int64_t sub_cnt = (int64_t)(spk >> 32);
+    const int64_t sub_edges = (int64_t)(spk & 0xFFFFFFFFull);
+    if (sub_cnt > p.list_cap) { ctl->error |= kErrCapacity; sub_cnt = p.list_cap; }
+    const uint32_t kind = ctl->hp_kind;
+    const int64_t step_edges = kind == 1u ? (int64_t)ctl->in_edges - sub_edges : (int64_t)ctl->in_edges;
+    trace_append(ctl, kind == 1u ? kModeHpSub : kModeHpWd, ctl->in_cnt, step_edges);
+    ctl->relaxed += (unsigned long long)step_edges;
+    ctl->step += 1;
+    ctl->blocks_done = 0;
+    const int64_t thr = p.hp_threshold;
+    if (kind == 1u && sub_cnt > 0) {
+        const uint32_t so = ctl->hp_from == kHpFromSuper ? 0u : (ctl->sub_in ^ 1u);
+        p.subs[so].scan[sub_cnt] = sub_edges;
+        ctl->hp_from = kHpFromSub;
+        ctl->sub_in = so;
+        ctl->in_cnt = (uint32_t)sub_cnt;
+        ctl->in_edges = (uint64_t)sub_edges;
+        ctl->sub_pack = 0ull;
+        ctl->hp_sub += 1;
+        ctl->hp_kind = (thr > 0 && sub_cnt < thr) ? 2u : 1u;
+        set_loop(p, ctl, true);
+    } else {
+        int64_t cnt = (int64_t)(pk >> 32);
+        const int64_t edges = (int64_t)(pk & 0xFFFFFFFFull);
+        if (cnt > p.list_cap) { ctl->error |= kErrCapacity; cnt = p.list_cap; }
+        const uint32_t out = ctl->par ^ 1u;
+        p.lists[out].scan[cnt] = edges;
+        ctl->par = out;
+        ctl->in_cnt = (uint32_t)cnt;
+        ctl->in_edges = (uint64_t)edges;
+        ctl->out_pack = 0ull;
+        ctl->sub_pack = 0ull;
+        ctl->level += 1;
+        ctl->hp_from = kHpFromSuper;
+        ctl->hp_sub = 0;
+        ctl->hp_kind = (thr > 0 && cnt < thr) ? 2u : 1u;
+        set_loop(p, ctl, cnt > 0);
+    }
+    __threadfence();
+}
+
+template <bool SSSP, int ITEMS>
+__global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];   // updated nodes -> next super list
+    __shared__ WarpBuf s_sb[kWarps];   // unfinished nodes -> next sub-list
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const uint32_t par = ctl->par;
+    const int64_t in_cnt = ctl->in_cnt;
+    const int64_t E = (int64_t)ctl->in_edges;
+    const uint32_t level = ctl->level;
+    const uint32_t stamp = ctl->epoch_base + level;
+    const uint32_t kind = ctl->hp_kind;
+    const uint32_t from = ctl->hp_from;
+    const uint32_t sub_in = ctl->sub_in;
+    uint32_t *status = ctl->status;
+    const NodeList in = from == kHpFromSuper ? p.lists[par] : p.subs[sub_in];
+    FlushOut osup;
+    osup.list = p.lists[par ^ 1u];
+    osup.elist = nullptr;
+    osup.pack = &ctl->out_pack;
+    osup.cap = p.list_cap;
+    osup.tile_cap = p.tile_cap;
+    osup.tile = p.tile;
+    osup.mdt = p.mdt;
+    FlushOut osub = osup;
+    osub.list = p.subs[from == kHpFromSuper ? 0u : (sub_in ^ 1u)];
+    osub.pack = &ctl->sub_pack;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    WarpBuf &wb = s_wb[warp];
+    WarpBuf &sb = s_sb[warp];
+    WarpScratch &ws = s_ws[warp];
+    uint32_t cnt = 0, scnt = 0;
+    if (kind == 2u) {
+        wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
+    } else {
+        const int64_t mdt = p.mdt;
+        const int64_t stride = (int64_t)gridDim.x * kBlock;
+        for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
+            const int64_t i = base + lane;
+            int64_t cur = 0, end = 0, rest = 0;
+            uint32_t du = 0;
+            int32_t u = 0;
+            if (i < in_cnt) {
+                cur = __ldg(in.beg + i);
+                const int64_t len = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
+                if (cur < 0 || len < 0 || cur + len > p.g.m) {
+                    atomicOr(&ctl->error, kErrBounds);
+                    cur = 0;
+                } else {
+                    const int64_t take = len < mdt ? len : mdt;
+                    end = cur + take;
+                    rest = len - take;
+                    u = __ldg(in.v + i);
+                    if (SSSP) du = status[u];
+                }
+            }
+            wpush(sb, scnt, rest > 0, u, end, (uint32_t)rest);
+            if (scnt > kWB - 32) wflush<kOutNode, true>(sb, ws, scnt, osub, ctl);
+            while (__any_sync(kFull, cur < end)) {
+                bool want = false;
+                int32_t v = 0;
+                int64_t vb = 0;
+                uint32_t vd = 0;
+                if (cur < end) {
+                    v = __ldg(p.g.col + cur);
+                    const bool hit = SSSP ? sssp_relax(status, p.epoch, v, du, __ldg(p.g.w + cur), stamp, ctl)
+                                          : bfs_claim(p.bitmap, status, v, level + 1);
+                    if (hit) {
+                        vb = __ldg(p.g.off + v);
+                        vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
+                        want = vd > 0;
+                    }
+                    ++cur;
+                }
+                wpush(wb, cnt, want, v, vb, vd);
+                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, osup, ctl);
+            }
+        }
+    }
+    wflush<kOutNode, true>(wb, ws, cnt, osup, ctl);
+    wflush<kOutNode, true>(sb, ws, scnt, osub, ctl);
+    if (block_is_last(ctl) && threadIdx.x == 0) finish_hp_step(p, ctl);
+}
+
+}  // namespace lbk

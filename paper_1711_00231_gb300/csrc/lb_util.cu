@@ -1,0 +1,367 @@
+// Query set-up and tear-down kernels, one-time preprocessing (COO build,
+// MDT histogram, node-splitting counts, CSR validation), the parent-tree
+// pass, the workload-decomposition offset inspector, and the step-kernel
+// dispatcher.
+#include "lb_launch.h"
+#include "lb_device.cuh"
+
+namespace lbk {
+
+// ------------------------------------------------------------ dispatcher --
+
+cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, cudaStream_t st) {
+    switch (strategy) {
+        case LB_BS: return launch_step_entry(sssp, false, p, grid, st);
+        case LB_NS: return launch_step_entry(sssp, true, p, grid, st);
+        case LB_WD: return launch_step_wd(sssp, p, grid, st);
+        case LB_EP: return launch_step_ep(sssp, p, grid, st);
+        case LB_HP: return launch_step_hp(sssp, p, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int step_blocks_per_sm(int strategy, bool sssp) {
+    switch (strategy) {
+        case LB_BS: return occupancy_step_entry(sssp, false);
+        case LB_NS: return occupancy_step_entry(sssp, true);
+        case LB_WD: return occupancy_step_wd(sssp);
+        case LB_EP: return occupancy_step_ep(sssp);
+        case LB_HP: return occupancy_step_hp(sssp);
+        default: return 1;
+    }
+}
+
+// ------------------------------------------------------- query set-up --
+
+// Worklist entries the source contributes (its node, its granules, or its
+// edges) for the strategy's list kind.
+__device__ __forceinline__ int64_t source_units(int strategy, int64_t deg, int32_t mdt) {
+    if (deg == 0) return 0;
+    if (strategy == LB_EP) return deg;
+    if (strategy == LB_NS) return deg <= mdt ? 1 : (deg + mdt - 1) / mdt;
+    return 1;
+}
+
+__global__ void k_prepare(StepParams p, int32_t src, uint32_t *status, int kind, uint32_t max_levels,
+                          uint64_t max_steps, uint64_t time_limit_ns) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctl *c = p.ctl;
+    const int64_t deg = p.g.off[src + 1] - p.g.off[src];
+    c->status = status;
+    c->src = src;
+    c->kind = kind;
+    c->level = 0;
+    c->par = 0;
+    c->in_cnt = (uint32_t)source_units(p.strategy, deg, p.mdt);
+    c->in_edges = (uint64_t)deg;
+    c->out_pack = 0ull;
+    c->sub_pack = 0ull;
+    c->hp_from = kHpFromSuper;
+    c->hp_sub = 0;
+    c->sub_in = 0;
+    c->hp_kind = (p.hp_threshold > 0 && (int64_t)c->in_cnt < p.hp_threshold) ? 2u : 1u;
+    c->blocks_done = 0;
+    c->active = 1;
+    c->error = 0;
+    if (c->epoch_next == 0u || c->epoch_next > 0xF0000000u) {
+        c->epoch_reset = 1;
+        c->epoch_base = 1;
+    } else {
+        c->epoch_reset = 0;
+        c->epoch_base = c->epoch_next;
+    }
+    c->max_levels = max_levels;
+    c->max_steps = max_steps;
+    c->t_deadline = global_ns() + time_limit_ns;
+    c->step = 0;
+    c->relaxed = 0ull;
+    c->pushes = 0ull;
+    c->trace_len = 0;
+}
+
+__global__ void k_init(StepParams p) {
+    const Ctl *c = p.ctl;
+    const int32_t src = c->src;
+    const bool sssp = c->kind == 1;
+    uint32_t *status = c->status;
+    const int64_t n = p.g.n;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const bool reset_epoch = c->epoch_reset != 0;
+    for (int64_t i = tid; i < n; i += stride) {
+        status[i] = i == src ? 0u : kInf;
+        if (sssp && reset_epoch) p.epoch[i] = 0u;
+    }
+    if (!sssp) {
+        const int64_t words = (n + 31) / 32;
+        for (int64_t wd = tid; wd < words; wd += stride)
+            p.bitmap[wd] = wd == (src >> 5) ? (1u << (src & 31)) : 0u;
+    }
+    const int64_t beg = p.g.off[src];
+    const int64_t deg = p.g.off[src + 1] - beg;
+    if (p.strategy == LB_EP) {
+        for (int64_t j = tid; j < deg; j += stride) p.elist[0][j] = (int32_t)(beg + j);
+        return;
+    }
+    const NodeList L = p.lists[0];
+    if (p.strategy == LB_NS) {
+        const int64_t units = source_units(LB_NS, deg, p.mdt);
+        for (int64_t j = tid; j < units; j += stride) {
+            L.v[j] = src;
+            L.beg[j] = beg + j * p.mdt;
+            L.scan[j] = j * p.mdt;
+        }
+        if (tid == 0) L.scan[units] = deg;
+        return;
+    }
+    if (tid == 0) {
+        L.v[0] = src;
+        L.beg[0] = beg;
+        L.scan[0] = 0;
+        L.scan[deg > 0 ? 1 : 0] = deg;
+    }
+    if (L.tstart != nullptr) {
+        const int64_t tiles = (deg + p.tile - 1) / p.tile;
+        for (int64_t k = tid; k < tiles && k < p.tile_cap; k += stride) L.tstart[k] = 0;
+    }
+}
+
+// After the loop: an SSSP whose relaxations ever saturated reports overflow
+// iff some final distance is still the saturated value.
+__global__ void k_finish_query(StepParams p) {
+    Ctl *c = p.ctl;
+    if (!(c->error & kErrSaturated)) return;
+    const uint32_t *status = c->status;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.g.n; i += stride)
+        if (status[i] == kSat) {
+            atomicOr(&c->error, kErrOverflow);
+            return;
+        }
+}
+
+cudaError_t launch_prepare(const StepParams &p, int32_t src, uint32_t *status, int kind, uint32_t max_levels,
+                           uint64_t max_steps, uint64_t time_limit_ns, cudaStream_t st) {
+    k_prepare<<<1, 32, 0, st>>>(p, src, status, kind, max_levels, max_steps, time_limit_ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const StepParams &p, int grid, cudaStream_t st) {
+    k_init<<<grid, kBlock, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_query(const StepParams &p, cudaStream_t st) {
+    k_finish_query<<<256, kBlock, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------- one-time preprocessing --
+
+// COO source array (Sec. II-B: the edge-based method needs the source of
+// every edge): a warp per node writes its id over its edge range.
+__global__ void k_coo_build(GraphDev g, int32_t *coo_src) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (int64_t u = w0; u < g.n; u += warps) {
+        const int64_t b = g.off[u], e = g.off[u + 1];
+        for (int64_t j = b + lane; j < e; j += 32) coo_src[j] = (int32_t)u;
+    }
+}
+
+cudaError_t launch_coo_build(const GraphDev &g, int32_t *coo_src, cudaStream_t st) {
+    k_coo_build<<<1024, kBlock, 0, st>>>(g, coo_src);
+    return cudaGetLastError();
+}
+
+// MDT histogram (Sec. III-B).  scratch[0] = max degree, scratch[1..bins] =
+// bin heights.  result = {MDT, maxDeg, binIndex}.
+__global__ void k_max_degree(GraphDev g, unsigned long long *scratch) {
+    unsigned long long mx = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n; u += stride) {
+        const unsigned long long d = (unsigned long long)(g.off[u + 1] - g.off[u]);
+        mx = d > mx ? d : mx;
+    }
+    for (int k = 16; k > 0; k >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, mx, k);
+        mx = o > mx ? o : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&scratch[0], mx);
+}
+
+__global__ void k_degree_hist(GraphDev g, int32_t bins, unsigned long long *scratch) {
+    extern __shared__ unsigned int sh[];
+    for (int k = threadIdx.x; k < bins; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const int64_t maxd = (int64_t)scratch[0];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (maxd > 0)
+        for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n; u += stride) {
+            const int64_t d = g.off[u + 1] - g.off[u];
+            if (d == 0) continue;
+            const int64_t k = (d * bins + maxd - 1) / maxd;  // 1-based bin: (k-1) max < d bins <= k max
+            atomicAdd(&sh[k - 1], 1u);
+        }
+    __syncthreads();
+    for (int k = threadIdx.x; k < bins; k += blockDim.x)
+        if (sh[k]) atomicAdd(&scratch[1 + k], (unsigned long long)sh[k]);
+}
+
+__global__ void k_mdt_pick(int32_t bins, const unsigned long long *scratch, int64_t *result) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t maxd = (int64_t)scratch[0];
+    if (maxd == 0) {
+        result[0] = 0;
+        result[1] = 0;
+        result[2] = 0;
+        return;
+    }
+    int32_t best = 1;
+    for (int32_t k = 2; k <= bins; ++k)
+        if (scratch[k] > scratch[best]) best = k;
+    int64_t mdt = ((int64_t)best * maxd) / bins;
+    result[0] = mdt < 1 ? 1 : mdt;
+    result[1] = maxd;
+    result[2] = best;
+}
+
+cudaError_t launch_mdt(const GraphDev &g, int32_t bins, unsigned long long *scratch, int64_t *result,
+                       cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)(bins + 1), st);
+    if (e != cudaSuccess) return e;
+    k_max_degree<<<608, kBlock, 0, st>>>(g, scratch);
+    k_degree_hist<<<608, kBlock, sizeof(unsigned int) * (size_t)bins, st>>>(g, bins, scratch);
+    k_mdt_pick<<<1, 32, 0, st>>>(bins, scratch, result);
+    return cudaGetLastError();
+}
+
+// Child nodes node splitting creates at threshold mdt.
+__global__ void k_ns_count(GraphDev g, int32_t mdt, unsigned long long *out) {
+    unsigned long long s = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n; u += stride) {
+        const int64_t d = g.off[u + 1] - g.off[u];
+        if (d > mdt) s += (unsigned long long)((d + mdt - 1) / mdt - 1);
+    }
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(kFull, s, k);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+cudaError_t launch_ns_count(const GraphDev &g, int32_t mdt, unsigned long long *out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_ns_count<<<608, kBlock, 0, st>>>(g, mdt, out);
+    return cudaGetLastError();
+}
+
+// CSR shape check for graphs created from device arrays.
+__global__ void k_validate(GraphDev g, uint32_t *err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0 && (g.off[0] != 0 || g.off[g.n] != g.m)) atomicOr(err, kErrShape);
+    for (int64_t u = tid; u < g.n; u += stride)
+        if (g.off[u + 1] < g.off[u]) atomicOr(err, kErrShape);
+    for (int64_t e = tid; e < g.m; e += stride) {
+        const int32_t v = g.col[e];
+        if (v < 0 || (int64_t)v >= g.n) atomicOr(err, kErrShape);
+        if (g.w != nullptr && g.w[e] == 0u) atomicOr(err, kErrZeroWeight);
+    }
+}
+
+cudaError_t launch_validate(const GraphDev &g, uint32_t *err, cudaStream_t st) {
+    k_validate<<<1216, kBlock, 0, st>>>(g, err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ parents --
+
+__global__ void k_parents_init(StepParams p, int32_t *parents) {
+    const int32_t src = p.ctl->src;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.g.n; i += stride)
+        parents[i] = i == src ? src : -1;
+}
+
+// Every reached u offers itself as parent of each out-neighbour v whose
+// value it explains exactly (level[u] + 1, or min(dist[u] + w, saturated)).
+// Any such u is a valid parent; with positive weights (and for BFS) the
+// values strictly increase along parents, so the result is a tree.
+template <bool SSSP>
+__global__ void k_parents(StepParams p, int32_t *parents) {
+    const uint32_t *status = p.ctl->status;
+    const int32_t src = p.ctl->src;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const uint32_t lane = threadIdx.x & 31u;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < p.g.n; u += warps) {
+        const uint32_t du = status[u];
+        if (du == kInf) continue;
+        const int64_t b = p.g.off[u], e = p.g.off[u + 1];
+        for (int64_t j = b + lane; j < e; j += 32) {
+            const int32_t v = p.g.col[j];
+            if (v == src) continue;
+            uint32_t want;
+            if (SSSP) {
+                const uint64_t a = (uint64_t)du + p.g.w[j];
+                want = a >= kSat ? kSat : (uint32_t)a;
+            } else {
+                want = du + 1;
+            }
+            if (status[v] == want) parents[v] = (int32_t)u;
+        }
+    }
+}
+
+cudaError_t launch_parents(const StepParams &p, bool sssp, int32_t *parents, cudaStream_t st) {
+    k_parents_init<<<608, kBlock, 0, st>>>(p, parents);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (sssp) k_parents<true><<<1216, kBlock, 0, st>>>(p, parents);
+    else k_parents<false><<<1216, kBlock, 0, st>>>(p, parents);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------- WD offsets inspection --
+
+// Pushes the F given entries, in order, through the production warp push
+// buffer with tile = edgesPerThread = ceil(sum / T); the tile starts the
+// flush writes are the per-thread NodeOffsets of Sec. III-A.
+__global__ void k_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList list, Ctl *ctl, int64_t *ept_out) {
+    __shared__ WarpBuf wb;
+    __shared__ WarpScratch ws;
+    const uint32_t lane = lane_id();
+    int64_t E = 0;
+    for (int64_t i = lane; i < F; i += 32) E += deg[i];
+    for (int k = 16; k > 0; k >>= 1) E += __shfl_xor_sync(kFull, E, k);
+    const int64_t ept = (E + T - 1) / T;
+    if (lane == 0) *ept_out = ept;
+    if (ept == 0) return;
+    FlushOut o;
+    o.list = list;
+    o.elist = nullptr;
+    o.pack = &ctl->out_pack;
+    o.cap = F;
+    o.tile_cap = T + 1;
+    o.tile = (int32_t)ept;
+    o.mdt = 1;
+    uint32_t cnt = 0;
+    for (int64_t c = 0; c < F; c += 32) {
+        const int64_t i = c + lane;
+        const bool want = i < F;
+        wpush(wb, cnt, want, want ? (int32_t)i : 0, 0, want ? (uint32_t)deg[i] : 0u);
+        if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o, ctl);
+    }
+    wflush<kOutNode, true>(wb, ws, cnt, o, ctl);
+    if (lane == 0) list.scan[F] = E;
+}
+
+cudaError_t launch_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList list, Ctl *ctl, int64_t *ept_out,
+                              cudaStream_t st) {
+    k_wd_offsets<<<1, 32, 0, st>>>(deg, F, T, list, ctl, ept_out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbk

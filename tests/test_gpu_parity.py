@@ -1,0 +1,346 @@
+"""GPU parity: every strategy's BFS levels and SSSP distances, computed by
+the CUDA kernels through the C ABI, must equal the CPU oracle's bit for bit
+(the shortest-path values are unique, so every schedule must agree).
+Parent trees are checked for validity only."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from paper_1711_00231_gb300 import lb
+
+pytestmark = pytest.mark.gpu
+
+STRATS = ["BS", "EP", "WD", "NS", "HP"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1711_00231_gb300 import _build
+    _build.build()
+
+
+def expected_iterations(g, lev):
+    """Worklist iterations of a level-synchronous BFS whose lists hold only
+    vertices with out-edges: one per level up to the deepest such vertex."""
+    live = (lev >= 0) & (g.degrees() > 0)
+    return 1 + (int(lev[live].max()) if live.any() else 0)
+
+
+def run_all(g, srcs, strategies=STRATS, sssp=True, options=None):
+    G = lb.Graph.from_csr(g)
+    if options:
+        G.set_options(**options)
+    try:
+        for src in srcs:
+            ref_lev, nlev = oracle.bfs(g, src)
+            for s in strategies:
+                lev = G.bfs(src, s)
+                assert np.array_equal(lev, ref_lev), f"BFS {s} src={src}: {np.flatnonzero(lev != ref_lev)[:10]}"
+                st = G.stats()
+                assert st["status"] == 0
+                assert st["iterations"] == expected_iterations(g, ref_lev), (s, st, nlev)
+            if sssp and g.weights is not None:
+                ref, ov = oracle.dijkstra(g, src)
+                for s in strategies:
+                    d, rc = G.sssp(src, s)
+                    assert rc == (lb.LB_ERR_OVERFLOW if ov else lb.LB_OK)
+                    assert np.array_equal(d, ref), f"SSSP {s} src={src}: {np.flatnonzero(d != ref)[:10]}"
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tiny_random_graphs(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 70))
+    m = int(rng.integers(0, 5 * n + 1))
+    src = rng.integers(0, n, m)
+    dst = rng.integers(0, n, m)
+    w = rng.integers(0 if seed % 3 == 0 else 1, 30, m)
+    g = gg.from_edges(n, src, dst, w, clean=bool(seed % 2))
+    run_all(g, sorted({0, n - 1, int(rng.integers(0, n))}))
+
+
+def test_rmat14_vertex0_all_strategies():
+    # R-MAT scale 14, edge factor 16, a/b/c/d = .57/.19/.19/.05, seed 1; BFS from 0
+    g = gg.rmat(14, 16, seed=1)
+    run_all(g, [0, gg.max_degree_vertex(g)] + gg.pick_sources(g, 3, seed=1).tolist())
+
+
+def test_rmat14_options():
+    g = gg.rmat(14, 16, seed=1)
+    for opts in [dict(wd_tile=256), dict(wd_tile=8192), dict(hp_threshold=-1), dict(hp_threshold=4),
+                 dict(mdt_override=1), dict(mdt_override=7), dict(loop_mode=1), dict(ctas_per_sm=1),
+                 dict(hist_bins=3)]:
+        run_all(g, [0, 17], options=opts)
+
+
+def test_grid_closed_form_and_oracle():
+    R, C = 96, 80
+    g = gg.grid(R, C, seed=1)
+    r, c = np.divmod(np.arange(R * C), C)
+    G = lb.Graph.from_csr(g)
+    try:
+        for s in STRATS:
+            assert np.array_equal(G.bfs(0, s), (r + c).astype(np.int32))
+    finally:
+        G.close()
+    run_all(g, [0, R * C - 1, (R // 2) * C + C // 3])
+
+
+def test_edge_cases():
+    # single vertex, no edges
+    g1 = gg.from_edges(1, [], [], [])
+    run_all(g1, [0])
+    # source without out-edges in a graph with edges
+    g2 = gg.from_edges(5, [1, 2, 3], [2, 3, 4], [1, 2, 3])
+    run_all(g2, [0, 1, 4])
+    # self-loops and multi-edges with different weights kept
+    g3 = gg.from_edges(4, [0, 0, 0, 1, 1, 2, 3], [0, 1, 1, 2, 2, 3, 3], [5, 9, 2, 4, 1, 7, 1], clean=False)
+    run_all(g3, [0, 1, 3])
+    # a star whose hub far exceeds every tile and MDT
+    n = 20000
+    g4 = gg.from_edges(n, np.zeros(n - 1, int), np.arange(1, n), np.arange(1, n) % 97 + 1)
+    run_all(g4, [0, 5])
+    # a long path: one vertex per level
+    n = 3000
+    g5 = gg.from_edges(n, np.arange(n - 1), np.arange(1, n), np.full(n - 1, 3))
+    run_all(g5, [0, 1500])
+
+
+def test_overflow_reported_and_saturated_values_match():
+    big = 0x80000000
+    g = gg.from_edges(5, [0, 1, 2, 0], [1, 2, 3, 4], [big, big - 3, 5, 1])
+    ref, ov = oracle.dijkstra(g, 0)
+    assert ov
+    G = lb.Graph.from_csr(g)
+    try:
+        for s in STRATS:
+            d, rc = G.sssp(0, s)
+            assert rc == lb.LB_ERR_OVERFLOW and np.array_equal(d, ref)
+        g_ok = gg.from_edges(3, [0, 1], [1, 2], [big, big - 3])
+        G2 = lb.Graph.from_csr(g_ok)
+        d, rc = G2.sssp(0, "WD")
+        assert rc == lb.LB_OK and d.tolist() == [0, big, 0xFFFFFFFD]
+        G2.close()
+    finally:
+        G.close()
+
+
+def test_unweighted_graph_rejects_sssp():
+    g = gg.rmat(10, 8, weights=None)
+    G = lb.Graph.from_csr(g)
+    try:
+        with pytest.raises(lb.LbError) as ei:
+            G.sssp(0, "WD")
+        assert ei.value.status == lb.LB_ERR_UNSUPPORTED
+    finally:
+        G.close()
+
+
+def test_rmat20_bfs_sssp_all_strategies():
+    # R-MAT scale 20, edge factor 16, weights U[1,255], source = highest-degree vertex
+    g = gg.rmat(20, 16, seed=1)
+    run_all(g, [gg.max_degree_vertex(g)])
+
+
+def test_grid4096_sssp_from_corner():
+    # 4096 x 4096 grid, weights U[1,1000], source at the corner
+    g = gg.grid(4096, 4096, seed=1)
+    ref, _ = oracle.dijkstra(g, 0)
+    G = lb.Graph.from_csr(g)
+    try:
+        for s in ["WD", "BS", "HP"]:
+            d, rc = G.sssp(0, s)
+            assert rc == lb.LB_OK and np.array_equal(d, ref), s
+        lev = G.bfs(0, "WD")
+        r, c = np.divmod(np.arange(g.n), 4096)
+        assert np.array_equal(lev, (r + c).astype(np.int32))
+        assert G.stats()["iterations"] == 8191
+    finally:
+        G.close()
+
+
+def test_parents_are_valid_trees():
+    import torch
+    g = gg.rmat(14, 16, seed=3)
+    G = lb.Graph.from_csr(g)
+    try:
+        for s in STRATS:
+            for src in [0, 11]:
+                lev = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                par = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                G.bfs_dev(src, s, lev, par)
+                torch.cuda.synchronize()
+                lv, pv = lev.cpu().numpy(), par.cpu().numpy()
+                ref, _ = oracle.bfs(g, src)
+                assert np.array_equal(lv, ref)
+                assert oracle.check_parents(g, src, lv, pv, unit=True) == 0
+                dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                G.sssp_dev(src, s, dist, par)
+                torch.cuda.synchronize()
+                dv = dist.cpu().numpy().view(np.uint32)
+                refd, _ = oracle.dijkstra(g, src)
+                assert np.array_equal(dv, refd)
+                assert oracle.check_parents(g, src, dv, par.cpu().numpy()) == 0
+                assert G.stats()["status"] == 0
+    finally:
+        G.close()
+
+
+def test_device_created_graph_matches():
+    import torch
+    g = gg.rmat(12, 8, seed=9)
+    off = torch.from_numpy(g.offsets).cuda()
+    col = torch.from_numpy(g.cols).cuda()
+    w = torch.from_numpy(g.weights.view(np.int32)).cuda()
+    G = lb.Graph(off, col, w, g.n, g.m, device_arrays=True)
+    try:
+        for s in STRATS:
+            assert np.array_equal(G.bfs(3, s), oracle.bfs(g, 3)[0])
+            assert np.array_equal(G.sssp(3, s)[0], oracle.dijkstra(g, 3)[0])
+    finally:
+        G.close()
+    bad = torch.from_numpy(np.where(g.cols == 5, g.n + 2, g.cols).astype(np.int32)).cuda()
+    with pytest.raises(lb.LbError):
+        lb.Graph(off, bad, None, g.n, g.m, device_arrays=True)
+
+
+# ------------------------------------------------- schedule artefacts
+
+
+@pytest.mark.parametrize("bins", [1, 3, 10, 64])
+def test_mdt_matches_oracle(bins):
+    for g in [gg.rmat(14, 16, seed=1), gg.grid(50, 70), gg.erdos_renyi(5000, 20000, seed=4),
+              gg.from_edges(4, [], [], [])]:
+        G = lb.Graph.from_csr(g)
+        try:
+            assert G.mdt(bins) == oracle.mdt(g.offsets, bins)[:3]
+        finally:
+            G.close()
+
+
+def test_wd_offsets_paper_example_and_random():
+    ept, no, eo = lb.lb_wd_offsets([5, 7], 4)
+    r_ept, r_no, r_eo = oracle.wd_offsets([5, 7], 4)
+    assert ept == r_ept == 3 and np.array_equal(no, r_no) and np.array_equal(eo, r_eo)
+    assert (no[1], eo[1]) == (0, 3)   # thread 2: edges 4-5 of node 1, then node 8
+    rng = np.random.default_rng(0)
+    for trial in range(20):
+        F = int(rng.integers(0, 3000))
+        deg = rng.integers(0, 50, F) * (rng.random(F) < 0.8)
+        deg[rng.random(F) < 0.01] = 5000
+        for T in [1, 2, 7, 64, 1000, 4096]:
+            a = lb.lb_wd_offsets(deg, T)
+            b = oracle.wd_offsets(deg, T)
+            assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]), (trial, T)
+
+
+def _two_node_frontier_graph(d1=5, d2=7):
+    # 0 -> {1, 8}; node 1 has d1 out-edges and node 8 has d2, to fresh leaves
+    leaves1 = list(range(9, 9 + d1))
+    leaves8 = list(range(9 + d1, 9 + d1 + d2))
+    src = [0, 0] + [1] * d1 + [8] * d2
+    dst = [1, 8] + leaves1 + leaves8
+    n = 9 + d1 + d2
+    return gg.from_edges(n, src, dst, np.ones(len(src), int))
+
+
+def test_hp_trace_matches_paper_example():
+    g = _two_node_frontier_graph()
+    G = lb.Graph.from_csr(g)
+    try:
+        G.set_options(mdt_override=3, hp_threshold=-1)
+        for kind in ("bfs", "sssp"):
+            if kind == "bfs":
+                G.bfs(0, "HP")
+            else:
+                G.sssp(0, "HP")
+            tr = G.trace()
+            lvl1 = tr[tr["level"] == 1]
+            ls, ed, md = oracle.hp_schedule([5, 7], 3, threshold=0)
+            assert lvl1["list_size"].tolist() == ls.tolist() == [2, 2, 1]
+            assert lvl1["edges"].tolist() == ed.tolist() == [6, 5, 1]
+            assert (lvl1["mode"] == 1).all()
+        # with the paper's switch to WD at the block size the two-node list is
+        # processed in one WD step
+        G.set_options(mdt_override=3, hp_threshold=1024)
+        G.bfs(0, "HP")
+        tr = G.trace()
+        lvl1 = tr[tr["level"] == 1]
+        ls, ed, md = oracle.hp_schedule([5, 7], 3, threshold=1024)
+        assert lvl1["mode"].tolist() == [2] and lvl1["edges"].tolist() == ed.tolist() == [12]
+    finally:
+        G.close()
+
+
+def test_hp_trace_matches_oracle_on_rmat():
+    g = gg.rmat(14, 16, seed=2)
+    G = lb.Graph.from_csr(g)
+    try:
+        mdt = oracle.mdt(g.offsets, 10)[0]
+        for thr in (-1, 64, 1024):
+            G.set_options(hp_threshold=thr)
+            lev = G.bfs(0, "HP")
+            tr = G.trace()
+            deg = g.degrees()
+            for L in np.unique(tr["level"]):
+                front = np.flatnonzero((lev == L) & (deg > 0))
+                ls, ed, md = oracle.hp_schedule(deg[front], mdt, threshold=max(thr, 0))
+                rows = tr[tr["level"] == L]
+                assert rows["list_size"].tolist() == ls.tolist(), (thr, L)
+                assert rows["edges"].tolist() == ed.tolist(), (thr, L)
+                assert rows["mode"].tolist() == [1 if x == 0 else 2 for x in md.tolist()]
+    finally:
+        G.close()
+
+
+def test_ns_granules_match_paper_example():
+    # node 8 with 7 out-edges at MDT 4 is served as two granules of 4 and 3
+    g = _two_node_frontier_graph(5, 7)
+    G = lb.Graph.from_csr(g)
+    try:
+        G.set_options(mdt_override=4)
+        G.bfs(0, "NS")
+        tr = G.trace()
+        lvl1 = tr[tr["level"] == 1]
+        runs = [len(oracle.ns_chunks(5, 4)), len(oracle.ns_chunks(7, 4))]
+        assert runs == [2, 2]
+        assert lvl1["list_size"].tolist() == [sum(runs)] and lvl1["edges"].tolist() == [12]
+        rep = G.mem_report("NS")
+        assert rep["mdt"] == 4 and rep["ns_children"] == oracle.ns_split(g.offsets, 4)[0] == 2
+    finally:
+        G.close()
+
+
+def test_ns_children_match_oracle_on_rmat():
+    g = gg.rmat(16, 16, seed=1)
+    G = lb.Graph.from_csr(g)
+    try:
+        rep = G.mem_report("NS")
+        mdt = oracle.mdt(g.offsets, 10)[0]
+        assert rep["mdt"] == mdt
+        assert rep["ns_children"] == oracle.ns_split(g.offsets, mdt)[0]
+    finally:
+        G.close()
+
+
+def test_mem_report_accounting():
+    g = gg.rmat(14, 16, seed=1)
+    n, m = g.n, g.m
+    G = lb.Graph.from_csr(g)
+    try:
+        for s in STRATS:
+            rep = G.mem_report(s)
+            assert rep["base_total"] == 8 * (n + 1) + 4 * m + 4 * m
+            if s == "EP":
+                # Sec. II-B: a weighted COO graph is 3E 4-byte elements (src,
+                # dst, wt); the CSR cols / weights arrays serve as dst / wt
+                assert rep["coo_src"] + rep["csr_cols"] + rep["csr_weights"] == 3 * 4 * m
+                assert rep["coo_src"] + rep["csr_cols"] == 2 * 4 * m
+            G.bfs(0, s)
+            G.sssp(0, s)
+            assert G.mem_report(s)["resident"] >= rep["base_total"] + rep["extra_total"] - rep["status"]
+    finally:
+        G.close()
