@@ -1,0 +1,398 @@
+"""Benchmark: frontier BFS / SSSP GTEPS on R-MAT scale 24 (edge factor 32,
+a/b/c/d = .57/.19/.19/.05, weights U[1,255], seed 1) from 64 sources drawn
+uniformly among vertices with out-edges, on one GB300 per rank.
+
+One step = one BFS and one SSSP from each of the rank's 64 sources with the
+library's best strategy (workload decomposition).  value = traversed edges
+(m_reached per query, summed over every query of every rank) / the max over
+ranks of the device time of the K timed steps.  The graph (4.4 GB) is
+resident in HBM before timing; it is larger than L2, so no flush is needed.
+
+Also reported: per-strategy timings (BS, EP, WD, NS, HP) on a subset of the
+sources, the roofline of the dominant kernel, an end-to-end number through
+the host-buffer C-ABI calls, and the CPU oracle on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU runs are query replicas (torchrun, one rank per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS/SSSP GTEPS on 1 GB300, % of HBM roofline; batched queries/s, p99 latency"
+WORKLOAD = dict(workload="rmat24_ef32_64src", graph="R-MAT scale 24, edge factor 32, a/b/c/d=.57/.19/.19/.05, "
+                "self-loops and duplicates removed, weights U[1,255], seed 1", sources=64,
+                source_rule="uniform among out-degree>0 vertices, seed 1", kinds=["bfs", "sssp"],
+                l2="inputs larger than L2 (CSR 4.4 GB)")
+# Compulsory bytes per reached edge / vertex (BFS: col 4 + dst status 4;
+# offsets 16 + queue pop 4 + push 4 + level write 4.  SSSP adds the weight
+# and the source distance read.)
+BYTES = {"bfs": (8, 28), "sssp": (12, 32)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--edge-factor", type=int, default=32)
+    ap.add_argument("--sources", type=int, default=64)
+    ap.add_argument("--strategy", default="WD")
+    ap.add_argument("--compare-sources", type=int, default=4)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--loop-mode", type=int, default=0,
+                    help="0: device-resident loop (CUDA graph WHILE); 1: host loop (for per-kernel profiling)")
+    ap.add_argument("--kinds", default="bfs,sssp")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def m_reached_torch(out, deg_t):
+    import torch
+    reached = out != -1
+    return int(torch.where(reached, deg_t, 0).sum().item()), int(reached.sum().item())
+
+
+def cpu_baseline(g, srcs, budget_s):
+    """The oracle (single-threaded FIFO BFS / binary-heap Dijkstra) timed on
+    host cores over a bounded sample of the same queries."""
+    import oracle
+    done_e, t_total, used = 0, 0.0, []
+    for kind in ("bfs", "sssp"):
+        for s in srcs:
+            if t_total > budget_s:
+                break
+            t0 = time.perf_counter()
+            if kind == "bfs":
+                res, _ = oracle.bfs(g, int(s))
+            else:
+                res, _ = oracle.dijkstra(g, int(s))
+            dt = time.perf_counter() - t0
+            done_e += oracle.m_reached(g, res)
+            t_total += dt
+            used.append(f"{kind}:{int(s)}")
+            if kind == "bfs" and len([u for u in used if u.startswith("bfs")]) >= 2:
+                break
+    return {"value": done_e / t_total / 1e9 if t_total else None, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{len(used)} queries of the same workload ({', '.join(used)}), {t_total:.1f} s of CPU time",
+            "host_cores": os.cpu_count()}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, on this host's cores,
+    on the same workload; each step is one BFS + one SSSP query."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import graphgen as gg
+    import oracle
+    g = gg.rmat(args.scale, args.edge_factor, seed=1)
+    srcs = gg.pick_sources(g, args.sources, seed=1)
+
+    def step(i):
+        s = int(srcs[i % len(srcs)])
+        t0 = time.perf_counter()
+        lev, _ = oracle.bfs(g, s)
+        d, _ = oracle.dijkstra(g, s)
+        dt = time.perf_counter() - t0
+        return oracle.m_reached(g, lev) + oracle.m_reached(g, d), dt
+
+    for i in range(args.warmup):
+        step(i)
+    tot_e, tot_t = 0, 0.0
+    for i in range(args.steps):
+        e, dt = step(args.warmup + i)
+        tot_e += e
+        tot_t += dt
+    val = tot_e / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint32",
+            "data": "synthetic", "config": dict(WORKLOAD, reference="CPU oracle, one BFS + one SSSP per step"),
+            "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of one BFS + one SSSP from one source each"},
+            "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import graphgen as gg
+    from paper_1711_00231_gb300 import _build, lb
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    t0 = time.time()
+    g = gg.rmat(args.scale, args.edge_factor, seed=1)
+    t_gen = time.time() - t0
+    all_src = gg.pick_sources(g, args.sources * world, seed=1)
+    srcs = all_src[rank * args.sources:(rank + 1) * args.sources]
+    t0 = time.time()
+    G = lb.Graph.from_csr(g)
+    if args.loop_mode:
+        G.set_options(loop_mode=args.loop_mode)
+    t_upload = time.time() - t0
+    deg_t = torch.from_numpy(np.diff(g.offsets)).cuda()
+    stream = torch.cuda.current_stream()
+    n = g.n
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    kinds = tuple(k for k in args.kinds.split(",") if k)
+    strat = args.strategy
+
+    def query(kind, s, strategy=strat):
+        if kind == "bfs":
+            G.bfs_dev(int(s), strategy, out, None, stream)
+        else:
+            G.sssp_dev(int(s), strategy, out, None, stream)
+
+    # work per query (edges and vertices reached), from a first run
+    work = {}
+    for kind in kinds:
+        for s in srcs:
+            query(kind, s)
+            torch.cuda.synchronize()
+            st = G.stats()
+            if st["status"] != 0:
+                raise SystemExit(f"query failed: {kind} src={s} status={st['status']}")
+            work[(kind, int(s))] = m_reached_torch(out, deg_t) + (st["steps"],)
+    ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
+          for k in kinds}
+
+    def step(record=False):
+        for kind in kinds:
+            for i, s in enumerate(srcs):
+                if record:
+                    ev[kind][i][0].record(stream)
+                query(kind, s)
+                if record:
+                    ev[kind][i][1].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    per_query_ms = {k: np.zeros(len(srcs)) for k in kinds}
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+        torch.cuda.synchronize()
+        for kind in kinds:
+            for i in range(len(srcs)):
+                per_query_ms[kind][i] += ev[kind][i][0].elapsed_time(ev[kind][i][1])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    # device time of the queries themselves (the host sync between steps excluded)
+    dev_ms = float(sum(per_query_ms[k].sum() for k in kinds))
+    t_ms = dev_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    edges_rank = sum(work[(k, int(s))][0] for k in kinds for s in srcs) * args.steps
+    edges_all = edges_rank
+    if world > 1:
+        te = torch.tensor([edges_rank], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(te)
+        edges_all = float(te.item())
+    value = edges_all / (t_ms / 1e3) / 1e9
+
+    res = {}
+    for kind in kinds:
+        e = sum(work[(kind, int(s))][0] for s in srcs) * args.steps
+        v = sum(work[(kind, int(s))][1] for s in srcs) * args.steps
+        t = per_query_ms[kind].sum() / 1e3
+        be, bv = BYTES[kind]
+        res[kind] = {"gteps": e / t / 1e9, "ms_per_query": 1e3 * t / (args.steps * len(srcs)),
+                     "algorithmic_gbs": (be * e + bv * v) / t / 1e9,
+                     "launches": sum(work[(kind, int(s))][2] + 3 for s in srcs) * args.steps}
+    peak, peak_kind = measured_peak()
+    dom = max(kinds, key=lambda k: per_query_ms[k].sum())
+    achieved = res[dom]["algorithmic_gbs"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"k_step_wd ({dom})", "peak_source": f"{peak_kind} hbm_gbs",
+                "unit_of_work": "one query (all its relax launches + set-up); algorithmic bytes per query "
+                                f"= {BYTES[dom][0]} B x m_reached + {BYTES[dom][1]} B x n_reached"}
+
+    extra = {}
+    if rank == 0 and not args.no_compare:
+        cmp_src = srcs[:args.compare_sources]
+        for kind in kinds:
+            row = {}
+            for s_name in ("BS", "EP", "WD", "NS", "HP"):
+                tot = 0.0
+                e_tot = 0
+                for s in cmp_src:
+                    query(kind, s, s_name)   # warm (builds its workspace / loop)
+                    torch.cuda.synchronize()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    query(kind, s, s_name)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    tot += a.elapsed_time(b)
+                    e_tot += work[(kind, int(s))][0]
+                    assert G.stats()["status"] == 0
+                row[s_name] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9}
+            row["speedup_wd_vs_bs"] = row["BS"]["ms_per_query"] / row["WD"]["ms_per_query"]
+            row["speedup_wd_vs_ep"] = row["EP"]["ms_per_query"] / row["WD"]["ms_per_query"]
+            extra[kind] = row
+        G.release()
+
+    # end to end through the host-buffer C-ABI calls (lb_bfs / lb_sssp):
+    # includes the D2H copy of every result into pinned host memory
+    e2e = None
+    if rank == 0:
+        host = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
+        hostu = host.view(np.uint32)
+        G.bfs(int(srcs[0]), strat)  # warm
+        t0 = time.perf_counter()
+        e_done = 0
+        for kind in kinds:
+            for s in srcs:
+                if kind == "bfs":
+                    lb.lb_bfs(G.h, int(s), strat, host)
+                else:
+                    lb.lb_sssp(G.h, int(s), strat, hostu)
+                e_done += work[(kind, int(s))][0]
+        dt = time.perf_counter() - t0
+        e2e = {"value": e_done / dt / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs) * len(kinds),
+               "d2h_bytes_per_step": 4 * n * len(srcs) * len(kinds),
+               "note": "graph resident; per query the source id goes in as a launch argument and the n x 4 B "
+                       "result comes back to pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(g, srcs[:2], args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
+                "config": dict(WORKLOAD, strategy=strat, parallelism=f"replicas{world}", n=g.n, m=g.m,
+                               scale=args.scale, edge_factor=args.edge_factor, sources=len(srcs), kinds=list(kinds),
+                               loop="device (CUDA graph WHILE)" if args.loop_mode == 0 else "host"),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": sum(res[k]["launches"] for k in kinds),
+                "per_kind": res, "strategies": extra,
+                "setup_s": {"generate": t_gen, "upload": t_upload}, "elapsed_ms_timed_region": elapsed_ms}
+        print(json.dumps(line), flush=True)
+    G.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
