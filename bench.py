@@ -255,7 +255,7 @@ def main():
             st = G.stats()
             if st["status"] != 0:
                 raise SystemExit(f"query failed: {kind} src={s} status={st['status']}")
-            work[(kind, int(s))] = m_reached_torch(out, deg_t) + (st["steps"],)
+            work[(kind, int(s))] = m_reached_torch(out, deg_t) + (st["steps"], st["iterations"], st["edges_relaxed"])
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
           for k in kinds}
 
@@ -317,7 +317,10 @@ def main():
         be, bv = BYTES[kind]
         res[kind] = {"gteps": e / t / 1e9, "ms_per_query": 1e3 * t / (args.steps * len(srcs)),
                      "algorithmic_gbs": (be * e + bv * v) / t / 1e9,
-                     "launches": sum(work[(kind, int(s))][2] + 3 for s in srcs) * args.steps}
+                     "launches": sum(work[(kind, int(s))][2] + 3 for s in srcs) * args.steps,
+                     "iterations_mean": float(np.mean([work[(kind, int(s))][3] for s in srcs])),
+                     "work_inflation": sum(work[(kind, int(s))][4] for s in srcs) / max(
+                         1, sum(work[(kind, int(s))][0] for s in srcs))}
     peak, peak_kind = measured_peak()
     dom = max(kinds, key=lambda k: per_query_ms[k].sum())
     achieved = res[dom]["algorithmic_gbs"]

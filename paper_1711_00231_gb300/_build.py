@@ -22,6 +22,11 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"
                      "--expt-relaxed-constexpr"]
 
 
+def _extra_flags() -> list:
+    """Extra nvcc flags from LB_NVCC_EXTRA (tuning builds, e.g. -DLB_WD_ITEMS=4)."""
+    return [f for f in os.environ.get("LB_NVCC_EXTRA", "").split() if f]
+
+
 def _nvcc() -> str:
     for c in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if c and os.path.exists(c):
@@ -31,7 +36,7 @@ def _nvcc() -> str:
 
 def _digest() -> str:
     h = hashlib.sha256()
-    h.update(" ".join(NVCC_FLAGS).encode())
+    h.update(" ".join(NVCC_FLAGS + _extra_flags()).encode())
     files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
     for f in files:
         with open(os.path.join(CSRC, f), "rb") as fh:
@@ -54,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *NVCC_FLAGS, *_extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

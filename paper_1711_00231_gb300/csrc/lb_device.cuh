@@ -181,6 +181,16 @@ __device__ __forceinline__ bool sssp_relax(uint32_t *__restrict__ status, uint32
     return atomicExch(&epoch[v], stamp) != stamp;
 }
 
+// SSSP: distance a worklist entry u relaxes with.  When u has already been
+// queued again in this iteration (its stamp is the current one), its
+// distance improved after it was listed and the next iteration expands it
+// with that newer value, so expanding it now is redundant work: return
+// kInf, which makes every relaxation from u a no-op.
+__device__ __forceinline__ uint32_t sssp_source_dist(const uint32_t *__restrict__ status,
+                                                     const uint32_t *__restrict__ epoch, int32_t u, uint32_t stamp) {
+    return epoch[u] == stamp ? kInf : status[u];
+}
+
 // ---- end-of-step protocol ----------------------------------------------------
 
 __device__ __forceinline__ bool block_is_last(Ctl *ctl) {

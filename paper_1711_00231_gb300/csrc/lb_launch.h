@@ -6,8 +6,14 @@
 
 namespace lbk {
 
-constexpr int kItemsWd = 4;  // edges per thread per round in WD tiles
-constexpr int kItemsEp = 4;  // worklist edges per thread per round in EP
+#ifndef LB_WD_ITEMS
+#define LB_WD_ITEMS 4
+#endif
+#ifndef LB_EP_ITEMS
+#define LB_EP_ITEMS 4
+#endif
+constexpr int kItemsWd = LB_WD_ITEMS;  // edges per thread per round in WD tiles
+constexpr int kItemsEp = LB_EP_ITEMS;  // worklist edges per thread per round in EP
 
 cudaError_t launch_step_entry(bool sssp, bool granules, const StepParams &p, int grid, cudaStream_t st);
 int occupancy_step_entry(bool sssp, bool granules);

@@ -8,6 +8,13 @@
 
 #include "lb_device.cuh"
 
+#ifndef LB_WD_MIN_BLOCKS
+#define LB_WD_MIN_BLOCKS 1
+#endif
+#ifndef LB_WD_WARP_LOOKUP
+#define LB_WD_WARP_LOOKUP 0
+#endif
+
 namespace lbk {
 
 // ---------------------------------------------------------------------------
@@ -51,7 +58,7 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
                 atomicOr(&ctl->error, kErrBounds);
                 cur = end = 0;
             } else if (SSSP) {
-                du = status[__ldg(in.v + i)];
+                du = sssp_source_dist(status, p.epoch, __ldg(in.v + i), stamp);
             }
         }
         while (__any_sync(kFull, cur < end)) {
@@ -82,9 +89,13 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
 // Workload decomposition over CTA tiles.  The input list's edges (in list
 // order) are cut into tiles of p.tile edges; tile t starts in entry
 // tstart[t] (written by the push that created the list).  Inside a tile,
-// consecutive threads take consecutive edges, so a node's adjacency is read
-// coalesced, and a thread finds the entry of each of its edges by a short
-// binary search over the tile's slice of the edge prefix.
+// consecutive lanes take consecutive edges, so a node's adjacency is read
+// coalesced.  A warp finds the entries of its 32 edges together: one
+// warp-uniform binary search over the tile's slice of the edge prefix gives
+// the entry of the first edge; every later entry that starts inside the
+// 32-edge window sets one bit of a mask (each entry has at least one edge,
+// so the window holds at most 32 starts), and a lane's entry is the first
+// one plus the number of starts at or before its position.
 // ---------------------------------------------------------------------------
 template <bool SSSP, int ITEMS>
 __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt,
@@ -92,6 +103,10 @@ __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const No
                                          uint32_t *status, uint32_t level, uint32_t stamp) {
     const int64_t T = p.tile;
     const int64_t ntiles = (E + T - 1) / T;
+    const uint32_t lane = lane_id();
+    const int64_t wbase = (int64_t)(threadIdx.x & ~31u);
+    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
+    (void)upto;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t e0 = t * T;
         const int64_t e1 = min(e0 + T, E);
@@ -108,22 +123,37 @@ __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const No
             bool ok[ITEMS];
 #pragma unroll
             for (int it = 0; it < ITEMS; ++it) {
-                const int64_t e = r0 + (int64_t)it * kBlock + threadIdx.x;
-                ok[it] = e < e1;
+                const int64_t ew = r0 + (int64_t)it * kBlock + wbase;  // the warp's first edge
+                const int64_t e = ew + lane;
+                ok[it] = false;
                 vv[it] = 0;
                 ww[it] = 0;
                 dd[it] = 0;
-                if (ok[it]) {
-                    const int64_t k = list_search(in.scan, i0, ihi, e);
-                    const int64_t eidx = __ldg(in.beg + k) + (e - __ldg(in.scan + k));
-                    if ((uint64_t)eidx >= (uint64_t)p.g.m) {
-                        atomicOr(&ctl->error, kErrBounds);
-                        ok[it] = false;
-                    } else {
-                        vv[it] = __ldg(p.g.col + eidx);
-                        if (SSSP) {
-                            ww[it] = __ldg(p.g.w + eidx);
-                            dd[it] = status[__ldg(in.v + k)];
+                if (ew < e1) {  // warp-uniform
+#if LB_WD_WARP_LOOKUP
+                    const int64_t kf = list_search(in.scan, i0, ihi, ew);
+                    const int64_t j = kf + 1 + lane;
+                    uint32_t bit = 0;
+                    if (j < ihi) {
+                        const int64_t pos = __ldg(in.scan + j) - ew;
+                        if (pos < 32) bit = 1u << pos;
+                    }
+                    const uint32_t starts = __reduce_or_sync(kFull, bit);
+                    const int64_t k = kf + __popc(starts & upto);
+#else
+                    const int64_t k = e < e1 ? list_search(in.scan, i0, ihi, e) : i0;
+#endif
+                    if (e < e1) {
+                        const int64_t eidx = __ldg(in.beg + k) + (e - __ldg(in.scan + k));
+                        if ((uint64_t)eidx >= (uint64_t)p.g.m) {
+                            atomicOr(&ctl->error, kErrBounds);
+                        } else {
+                            ok[it] = true;
+                            vv[it] = __ldg(p.g.col + eidx);
+                            if (SSSP) {
+                                ww[it] = __ldg(p.g.w + eidx);
+                                dd[it] = sssp_source_dist(status, p.epoch, __ldg(in.v + k), stamp);
+                            }
                         }
                     }
                 }
@@ -150,7 +180,7 @@ __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const No
 }
 
 template <bool SSSP, int ITEMS>
-__global__ void __launch_bounds__(kBlock) k_step_wd(StepParams p) {
+__global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams p) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
     Ctl *ctl = p.ctl;
@@ -227,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
                 vv[it] = __ldg(p.g.col + e);
                 if (SSSP) {
                     ww[it] = __ldg(p.g.w + e);
-                    dd[it] = status[__ldg(p.coo_src + e)];
+                    dd[it] = sssp_source_dist(status, p.epoch, __ldg(p.coo_src + e), stamp);
                 }
             }
         }
@@ -359,10 +389,13 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
                     end = cur + take;
                     rest = len - take;
                     u = __ldg(in.v + i);
-                    if (SSSP) du = status[u];
+                    if (SSSP) du = sssp_source_dist(status, p.epoch, u, stamp);
                 }
             }
-            wpush(sb, scnt, rest > 0, u, end, (uint32_t)rest);
+            // an entry skipped as redundant (SSSP, see sssp_source_dist) leaves no remainder
+            const bool keep = rest > 0 && (!SSSP || du != kInf);
+            if (SSSP && du == kInf) end = cur;
+            wpush(sb, scnt, keep, u, end, (uint32_t)rest);
             if (scnt > kWB - 32) wflush<kOutNode, true>(sb, ws, scnt, osub, ctl);
             while (__any_sync(kFull, cur < end)) {
                 bool want = false;
