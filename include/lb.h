@@ -215,6 +215,29 @@ lb_status lb_mdt(lb_graph *g, int32_t bins, int64_t *mdt, int64_t *max_degree, i
 lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_off, int64_t *edge_off,
                         int64_t *ept);
 
+/* ------------------------------------------------- no allocation --- */
+
+/* BFS with the workload-decomposition kernel for callers that cannot
+ * allocate device memory (the paper has no counterpart: it is an
+ * integration form).  Such callers include a process whose GPU memory is
+ * entirely owned by another allocator, such as a framework's caching pool,
+ * and a latency-bound service that must not call cudaMalloc once running,
+ * because cudaMalloc can block and synchronise the device.
+ *
+ * offsets_dev (n+1 int64), cols_dev (m int32) and levels_dev (n int32,
+ * receives hop counts, -1 unreachable) are caller-owned device pointers on
+ * the current device; no lb_graph is used and the CSR is not validated.
+ * All other memory comes from one fixed array of device memory inside the
+ * library (about 5.4 MiB; every GPU that loads the library holds it until
+ * the process exits), so the call allocates nothing.  Limits: n <= 131072
+ * and m <= 16777216; larger sizes return LB_ERR_ARG.  The first call on a
+ * device looks the array up (cudaGetSymbolAddress) and should come before
+ * any stream capture.  Every call shares the array; calls whose GPU work
+ * overlaps race and give wrong results.  The call waits for its result on
+ * `stream` (it reads the worklist size back every iteration). */
+lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t *cols_dev, int64_t n, int64_t m, int32_t src,
+                            int32_t *levels_dev, void *stream);
+
 /* ------------------------------------------------------------- misc --- */
 
 /* Device allocator hook used for every later allocation (NULL, NULL

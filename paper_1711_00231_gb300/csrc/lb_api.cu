@@ -525,6 +525,8 @@ lb_graph *new_graph(int64_t n, int64_t m, bool weighted) {
 
 }  // namespace
 
+void lbk::set_last_error(const char *msg) { t_err = msg; }
+
 extern "C" {
 
 const char *lb_last_error(void) { return t_err.c_str(); }

@@ -135,4 +135,7 @@ cudaError_t launch_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList
                               cudaStream_t st);
 cudaError_t launch_parents(const StepParams &p, bool sssp, int32_t *parents, cudaStream_t st);
 
+// Sets the message lb_last_error() returns on the calling thread.
+void set_last_error(const char *msg);
+
 }  // namespace lbk

@@ -92,6 +92,7 @@ def _load():
         "lb_mdt": ([P, i32, P, P, P], st),
         "lb_wd_offsets": ([P, i64, i64, P, P, P], st),
         "lb_set_allocator": ([P, P, P], st),
+        "lb_bfs_wd_noalloc": ([P, P, i64, i64, i32, P, P], st),
         "lb_last_error": ([], ctypes.c_char_p),
         "lb_version": ([], ctypes.c_char_p),
     }
@@ -256,6 +257,15 @@ def lb_wd_offsets(deg, T: int):
     ept = ctypes.c_int64()
     _check(_load().lb_wd_offsets(_ptr(d) if d.size else None, d.size, T, _ptr(no), _ptr(eo), ctypes.byref(ept)))
     return ept.value, no, eo
+
+
+def lb_bfs_wd_noalloc(offsets_dev, cols_dev, n: int, m: int, src: int, levels_dev, stream=None) -> None:
+    """BFS (workload decomposition) that allocates no device memory: for
+    callers whose GPU memory belongs to another allocator or that must not
+    call cudaMalloc while serving.  Scratch comes from a fixed array inside
+    the library; n <= 131072, m <= 16777216."""
+    _check(_load().lb_bfs_wd_noalloc(_ptr(offsets_dev), _ptr(cols_dev), n, m, src, _ptr(levels_dev),
+                                     _stream_handle(stream)))
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
