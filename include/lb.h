@@ -195,6 +195,14 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out);
 /* Releases every query workspace of g (the CSR stays). */
 lb_status lb_release_workspaces(lb_graph *g);
 
+/* Autotuner: times strategy s for `kind` from each of the nsrc sources
+ * under a grid of options (WD tile size 512..4096, CTAs per SM, and for HP
+ * the WD-switch threshold), keeps the fastest on g and returns it in *best
+ * with its mean query time in *best_ms (either may be NULL).  The other
+ * option fields are kept as they were. */
+lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *srcs, int32_t nsrc, lb_options *best,
+                      double *best_ms);
+
 /* ------------------------------------------ schedule artefacts --- */
 
 /* Histogram MDT (Sec. III-B, "Automatic Determination of Node Splitting
@@ -214,6 +222,68 @@ lb_status lb_mdt(lb_graph *g, int32_t bins, int64_t *mdt, int64_t *max_degree, i
  * *ept receives edgesPerThread.  Uses the current device; F, T <= 2^24. */
 lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_off, int64_t *edge_off,
                         int64_t *ept);
+
+/* ---------------------------------------------- batching / serving --- */
+
+/* Many BFS / SSSP queries over many resident graphs run in one persistent
+ * kernel (the paper runs one query at a time; batching is an addition).
+ * Each query in flight owns a slot (its own worklists, bitmap, stamps and
+ * loop state); the kernel's CTAs claim workload-decomposition tiles
+ * (Sec. III-A) of any slot's current iteration, so iterations of different
+ * queries interleave and finished slots take new requests at once
+ * (continuous batching).  Results equal the single-query calls exactly. */
+typedef struct lb_server lb_server;
+
+typedef struct lb_server_options {
+    int32_t slots;        /* queries in flight at most; 0 = as many as fit in
+                             mem_fraction of free HBM, at most 256 */
+    int32_t ctas_per_sm;  /* persistent grid: CTAs per SM (0 = occupancy) */
+    int32_t tile;         /* worklist edges per work tile (0 = 2048) */
+    int32_t idle_us;      /* the kernel exits after this long with no work
+                             (0 = 1000); it is relaunched on demand */
+    double mem_fraction;  /* share of free HBM the slots may take (0 = 0.5) */
+    int32_t reserved[8];
+} lb_server_options;
+
+typedef struct lb_server_info_t {
+    int32_t slots;            /* slots allocated (admission by free HBM) */
+    int32_t grid;             /* CTAs of the persistent kernel */
+    int64_t slot_bytes;       /* device bytes per slot */
+    int64_t slot_n;           /* largest vertex count a slot serves */
+    int64_t kernel_launches;  /* persistent-kernel launches so far */
+    int64_t submitted;
+    int64_t completed;        /* completions returned by lb_server_poll */
+} lb_server_info_t;
+
+typedef struct lb_completion {
+    uint64_t ticket;          /* from lb_server_submit */
+    int32_t status;           /* lb_status of the query */
+    int32_t graph;
+    int64_t iterations;       /* worklist iterations */
+    int64_t edges_relaxed;
+    int64_t device_ns;        /* admission to completion on the device */
+} lb_completion;
+
+/* graphs: ngraphs handles on the current device; they must outlive the
+ * server.  Slot workspaces are sized for the largest graph. */
+lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_server_options *opt,
+                           lb_server **out);
+lb_status lb_server_destroy(lb_server *s);
+lb_status lb_server_info(const lb_server *s, lb_server_info_t *info);
+
+/* Queues one query (non-blocking).  kind: LB_KIND_BFS / LB_KIND_SSSP;
+ * out_dev: n int32 / uint32 on the device, written when the query
+ * completes.  *ticket identifies its completion.  Fails with
+ * LB_ERR_UNSUPPORTED when 65536 queries are outstanding (poll first). */
+lb_status lb_server_submit(lb_server *s, int32_t graph, int32_t src, int32_t kind, void *out_dev, uint64_t *ticket);
+
+/* Returns up to cap completed queries (non-blocking), in completion order,
+ * and relaunches the persistent kernel if work is pending and it has left. */
+lb_status lb_server_poll(lb_server *s, lb_completion *out, int32_t cap, int32_t *ndone);
+
+/* Asks the persistent kernel to leave and waits for it (queries in flight
+ * stay in their slots and resume at the next submit / poll). */
+lb_status lb_server_stop(lb_server *s);
 
 /* ------------------------------------------------- no allocation --- */
 

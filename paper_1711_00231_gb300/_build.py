@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblb.so")
 
 SOURCES = ["lb_api.cu", "lb_util.cu", "lb_step_entry.cu", "lb_step_wd.cu", "lb_step_ep.cu", "lb_step_hp.cu",
-           "lb_noalloc.cu"]
+           "lb_noalloc.cu",
+           "lb_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE,
                      "--expt-relaxed-constexpr"]

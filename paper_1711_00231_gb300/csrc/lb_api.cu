@@ -5,6 +5,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lb_internal.cuh"
 
@@ -527,6 +528,12 @@ lb_graph *new_graph(int64_t n, int64_t m, bool weighted) {
 
 void lbk::set_last_error(const char *msg) { t_err = msg; }
 
+void lbk::graph_device_arrays(const lb_graph *g, const int64_t **off, const int32_t **col, const uint32_t **w) {
+    *off = g->off;
+    *col = g->col;
+    *w = g->w;
+}
+
 extern "C" {
 
 const char *lb_last_error(void) { return t_err.c_str(); }
@@ -764,6 +771,78 @@ lb_status lb_release_workspaces(lb_graph *g) {
     cudaStreamSynchronize(g->stream);
     free_workspace(g);
     g->has_last = false;
+    return LB_OK;
+}
+
+lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *srcs, int32_t nsrc, lb_options *best,
+                      double *best_ms) {
+    if (!g || !srcs || nsrc < 1 || nsrc > 1024) return fail(LB_ERR_ARG, "need a graph and 1..1024 sources");
+    if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP) return fail(LB_ERR_ARG, "bad kind");
+    if (s == LB_AUTO) s = LB_WD;
+    if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy");
+    for (int32_t i = 0; i < nsrc; ++i)
+        if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return fail(LB_ERR_ARG, "source out of range");
+    if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
+    const lb_options base = g->opt;
+    // candidate grid: tile sizes and grid shapes for every strategy, plus the
+    // HP list-size threshold where it matters
+    const int32_t tiles[] = {512, 1024, 2048, 4096};
+    const int32_t ctas[] = {0, 2, 3};
+    const int32_t thr[] = {256, 1024, 4096};
+    std::vector<lb_options> cands;
+    for (int32_t t : tiles)
+        for (int32_t c : ctas) {
+            if (s == LB_HP) {
+                for (int32_t h : thr) {
+                    lb_options o = base;
+                    o.wd_tile = t;
+                    o.ctas_per_sm = c;
+                    o.hp_threshold = h;
+                    cands.push_back(o);
+                }
+            } else if (s == LB_WD || s == LB_EP || c == 0 || t == 2048) {
+                lb_options o = base;
+                o.wd_tile = t;
+                o.ctas_per_sm = c;
+                cands.push_back(o);
+            }
+        }
+    double best_t = 1e300;
+    lb_options best_o = base;
+    uint32_t *out = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        DeviceGuard dg(g->device);
+        if (!g->out_internal) LB_TRY(g->alloc(&g->out_internal, g->n));
+        out = g->out_internal;
+    }
+    for (const lb_options &o : cands) {
+        LB_TRY(lb_set_options(g, &o));
+        double tot = 0.0;
+        bool ok = true;
+        for (int32_t i = 0; i < nsrc && ok; ++i) {
+            for (int rep = 0; rep < 2 && ok; ++rep) {  // first run builds the loop; the second is timed
+                lb_status st;
+                {
+                    std::lock_guard<std::mutex> lk(g->mu);
+                    DeviceGuard dg(g->device);
+                    st = run_query(g, kind, s, srcs[i], out, nullptr, g->stream);
+                }
+                if (st != LB_OK) return st;
+                lb_query_stats qs;
+                LB_TRY(lb_last_stats(g, &qs));
+                if (qs.status != LB_OK && qs.status != LB_ERR_OVERFLOW) ok = false;
+                if (rep == 1) tot += qs.device_ms;
+            }
+        }
+        if (ok && tot < best_t) {
+            best_t = tot;
+            best_o = o;
+        }
+    }
+    LB_TRY(lb_set_options(g, &best_o));
+    if (best) *best = best_o;
+    if (best_ms) *best_ms = best_t / nsrc;
     return LB_OK;
 }
 

@@ -45,6 +45,8 @@ struct FlushOut {
     NodeList list;     // node / granule output
     int32_t *elist;    // edge-id output
     unsigned long long *pack;
+    uint32_t *err;               // error word (capacity overflow)
+    unsigned long long *pushes;  // push counter
     int64_t cap;       // entries the output can hold
     int64_t tile_cap;  // tstart entries
     int32_t tile;
@@ -92,7 +94,7 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, ui
 
 // Warp-uniform flush of a warp push buffer into a global list.
 template <int KIND, bool TILED>
-__device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o, Ctl *ctl) {
+__device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
     if (cnt == 0) return;
     const uint32_t lane = lane_id();
     uint32_t run_u = 0, run_e = 0;
@@ -118,7 +120,7 @@ __device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const F
     const int64_t ubase = (int64_t)(old >> 32);
     const int64_t ebase = (int64_t)(old & 0xFFFFFFFFull);
     if (ubase + (int64_t)run_u > o.cap) {
-        if (lane == 0) atomicOr(&ctl->error, kErrCapacity);
+        if (lane == 0) atomicOr(o.err, kErrCapacity);
         cnt = 0;
         __syncwarp();
         return;
@@ -150,7 +152,7 @@ __device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const F
             }
         }
     }
-    if (lane == 0) atomicAdd(&ctl->pushes, (unsigned long long)run_u);
+    if (lane == 0) atomicAdd(o.pushes, (unsigned long long)run_u);
     cnt = 0;
     __syncwarp();
 }

@@ -138,4 +138,7 @@ cudaError_t launch_parents(const StepParams &p, bool sssp, int32_t *parents, cud
 // Sets the message lb_last_error() returns on the calling thread.
 void set_last_error(const char *msg);
 
+// Device CSR arrays of a graph (for the serving engine's graph table).
+void graph_device_arrays(const lb_graph *g, const int64_t **off, const int32_t **col, const uint32_t **w);
+
 }  // namespace lbk

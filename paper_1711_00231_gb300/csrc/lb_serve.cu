@@ -1,0 +1,872 @@
+// Batched / served queries: one persistent kernel runs many BFS / SSSP
+// queries over many resident graphs at once.
+//
+// Every query in flight owns a slot: its own worklists, visited bitmap,
+// stamps and loop state.  A slot always has at most one open job (reset its
+// output, relax one worklist iteration with workload-decomposition tiles,
+// or check for overflow), cut into tiles.  The CTAs of the persistent grid
+// scan the slots and claim tiles with one atomicAdd on the slot's claim word
+// (generation << 32 | next tile); the CTA that finishes a job's last tile
+// finalises it and opens the slot's next job, so iterations of different
+// queries interleave freely on the GPU and no grid-wide barrier exists.
+//
+// Requests arrive through a ring in pinned, device-mapped host memory: the
+// host writes a request and then bumps `submitted`; an idle CTA that wins
+// the admission lock moves pending requests into free slots.  Completions
+// go back through a second mapped ring (one record per query, published by
+// a sequence number written last).  The kernel leaves when it has had
+// nothing to do for idle_ns, when the host raises `stop`, or at a hard time
+// limit; the host relaunches it when work is pending and it has exited.
+//
+// All loads of data other CTAs write during the kernel (worklists, status,
+// bitmap, stamps) bypass L1 (ld.global.cg), because L1 is not coherent
+// within a kernel and slots are reused.
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "lb_device.cuh"
+
+namespace lbk {
+namespace srv {
+
+constexpr uint32_t kRing = 1u << 16;         // request / completion ring entries
+constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
+constexpr int kItems = 4;
+
+enum : uint32_t { kJobNone = 0, kJobInit = 1, kJobRelax = 2, kJobCheck = 3 };
+
+struct Req {
+    int32_t graph;
+    int32_t src;
+    int32_t kind;
+    int32_t pad;
+    unsigned long long out;
+    unsigned long long ticket;
+};
+
+struct Done {
+    unsigned long long ticket;
+    int32_t status;
+    int32_t graph;
+    uint32_t iterations;
+    uint32_t pad;
+    unsigned long long t_admit_ns;
+    unsigned long long t_done_ns;
+    unsigned long long edges_relaxed;
+    unsigned long long seq;  // written last: index + 1 once the record is complete
+};
+
+struct HostShared {
+    unsigned long long submitted;  // host: requests written
+    unsigned long long consumed;   // device: requests taken into slots
+    uint32_t stop;                 // host: leave the kernel
+    uint32_t pad;
+    Req req[kRing];
+    Done done[kRing];
+};
+
+struct Slot {
+    unsigned long long claim;  // generation << 32 | next tile
+    uint32_t job_gen;          // generation the job fields below belong to
+    uint32_t job_kind;
+    uint32_t job_tiles;
+    uint32_t job_done;
+    uint32_t busy;
+    int32_t graph;
+    int32_t src;
+    int32_t kind;
+    uint32_t level;
+    uint32_t par;
+    uint32_t in_cnt;
+    uint32_t error;
+    uint32_t epoch_base;
+    uint32_t epoch_next;
+    uint32_t epoch_reset;
+    uint64_t in_edges;
+    unsigned long long out_pack;
+    unsigned long long relaxed;
+    unsigned long long pushes;
+    unsigned long long ticket;
+    unsigned long long t_admit;
+    uint32_t *status;
+    uint32_t *bitmap;
+    uint32_t *epoch;
+    NodeList lists[2];
+};
+
+struct Shared {  // device-global control of the persistent kernel
+    uint32_t admit_lock;
+    uint32_t active;         // busy slots
+    uint32_t stopping;
+    uint32_t error;
+    unsigned long long consumed;
+    unsigned long long completed;
+    unsigned long long kernel_t0;
+};
+
+struct Params {
+    Slot *slots;
+    int32_t nslots;
+    int32_t ngraphs;
+    const GraphDev *graphs;
+    HostShared *host;  // device view of the mapped ring
+    Shared *sh;
+    int32_t tile;
+    int32_t pad;
+    int64_t slot_cap;   // worklist entries per slot list
+    int64_t tile_cap;   // tile starts per slot list
+    int64_t slot_n;     // largest n a slot serves
+    uint64_t idle_ns;
+    uint64_t hard_ns;
+};
+
+// ---- coherent (L2) loads and system-scope accesses ------------------------
+
+template <class T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_sys32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int64_t list_search_cg(const int64_t *scan, int64_t lo, int64_t hi, int64_t e) {
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldcg(scan + mid) <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool bfs_claim_cg(uint32_t *bitmap, uint32_t *status, int32_t v, uint32_t newlev) {
+    const uint32_t word = (uint32_t)v >> 5, bit = 1u << ((uint32_t)v & 31u);
+    if (__ldcg(bitmap + word) & bit) return false;
+    if (atomicOr(&bitmap[word], bit) & bit) return false;
+    status[v] = newlev;
+    return true;
+}
+
+__device__ __forceinline__ bool sssp_relax_cg(uint32_t *status, uint32_t *epoch, int32_t v, uint32_t du, uint32_t w,
+                                              uint32_t stamp, uint32_t *err) {
+    if (du == kInf) return false;
+    const uint64_t a64 = (uint64_t)du + (uint64_t)w;
+    const uint32_t alt = a64 >= kSat ? kSat : (uint32_t)a64;
+    if (alt >= __ldcg(status + v)) return false;
+    const uint32_t old = atomicMin(&status[v], alt);
+    if (alt >= old) return false;
+    if (alt == kSat) atomicOr(err, kErrSaturated);
+    if (__ldcg(epoch + v) == stamp) return false;
+    return atomicExch(&epoch[v], stamp) != stamp;
+}
+
+// Dynamic slot fields change between jobs and are written by other SMs, so
+// they are read through a volatile view (no L1); the pointer fields are
+// fixed at server creation.
+struct SlotState {
+    int32_t graph, src, kind;
+    uint32_t level, par, in_cnt, epoch_base, epoch_reset;
+    uint64_t in_edges;
+    uint32_t *status;
+};
+
+__device__ __forceinline__ SlotState slot_state(const Slot *S) {
+    const volatile Slot *V = S;
+    SlotState t;
+    t.graph = V->graph;
+    t.src = V->src;
+    t.kind = V->kind;
+    t.level = V->level;
+    t.par = V->par;
+    t.in_cnt = V->in_cnt;
+    t.epoch_base = V->epoch_base;
+    t.epoch_reset = V->epoch_reset;
+    t.in_edges = V->in_edges;
+    t.status = V->status;
+    return t;
+}
+
+// ---- jobs ------------------------------------------------------------------
+
+// Opens the slot's next job (single thread).  Parameters are written before
+// the claim word moves to the new generation.
+__device__ void open_job(Slot *S, uint32_t kind, uint32_t tiles) {
+    const unsigned long long w = atomicAdd(&S->claim, 0ull);
+    const uint32_t gen = (uint32_t)(w >> 32) + 1u;
+    S->job_gen = gen;
+    S->job_kind = kind;
+    S->job_tiles = tiles;
+    S->job_done = 0;
+    __threadfence();
+    atomicExch(&S->claim, (unsigned long long)gen << 32);
+}
+
+__device__ void complete_query(const Params &P, Slot *S, int32_t status_code) {
+    const unsigned long long idx = atomicAdd(&P.sh->completed, 1ull);
+    Done *d = &P.host->done[idx % kRing];
+    const volatile Slot *V = S;
+    d->ticket = V->ticket;
+    d->status = status_code;
+    d->graph = V->graph;
+    d->iterations = V->level;
+    d->t_admit_ns = V->t_admit;
+    d->t_done_ns = global_ns();
+    d->edges_relaxed = V->relaxed;
+    __threadfence_system();
+    st_release_sys(&d->seq, idx + 1ull);
+    S->epoch_next = V->epoch_base + V->level + 1;
+    S->job_kind = kJobNone;
+    S->job_tiles = 0;
+    __threadfence();
+    S->busy = 0;
+    atomicSub(&P.sh->active, 1u);
+}
+
+__device__ int32_t slot_status(const Slot *S) {
+    const uint32_t e = ((const volatile Slot *)S)->error;
+    if (e & (kErrCapacity | kErrShape | kErrBounds)) return LB_ERR_INTERNAL;
+    if (e & (kErrIterCap | kErrDeadline)) return LB_ERR_TIMEOUT;
+    if (e & kErrOverflow) return LB_ERR_OVERFLOW;
+    return LB_OK;
+}
+
+// Finalises the slot's job after its last tile (single thread).
+__device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
+    const SlotState st = slot_state(S);
+    const GraphDev g = P.graphs[st.graph];
+    const int64_t T = P.tile;
+    if (kind == kJobInit) {
+        const int64_t beg = g.off[st.src];
+        const int64_t deg = g.off[st.src + 1] - beg;
+        S->level = 0;
+        S->par = 0;
+        S->out_pack = 0ull;
+        S->relaxed = 0ull;
+        if (deg == 0) {
+            S->level = 1;
+            complete_query(P, S, LB_OK);
+            return;
+        }
+        NodeList L = S->lists[0];
+        L.v[0] = st.src;
+        L.beg[0] = beg;
+        L.scan[0] = 0;
+        L.scan[1] = deg;
+        const int64_t tiles = (deg + T - 1) / T;
+        for (int64_t k = 0; k < tiles && k < P.tile_cap; ++k) L.tstart[k] = 0;
+        S->in_cnt = 1;
+        S->in_edges = (uint64_t)deg;
+        open_job(S, kJobRelax, (uint32_t)tiles);
+        return;
+    }
+    if (kind == kJobRelax) {
+        const unsigned long long pk = ld_volatile(&S->out_pack);
+        int64_t cnt = (int64_t)(pk >> 32);
+        const int64_t edges = (int64_t)(pk & 0xFFFFFFFFull);
+        if (cnt > P.slot_cap) { atomicOr(&S->error, kErrCapacity); cnt = P.slot_cap; }
+        S->relaxed = ld_volatile(&S->relaxed) + st.in_edges;
+        S->level = st.level + 1;
+        const uint32_t out = st.par ^ 1u;
+        const uint32_t err = atomicOr(&S->error, 0u);
+        if (cnt > 0 && st.level + 1 <= (uint32_t)g.n && !(err & (kErrCapacity | kErrBounds))) {
+            S->lists[out].scan[cnt] = edges;
+            S->par = out;
+            S->in_cnt = (uint32_t)cnt;
+            S->in_edges = (uint64_t)edges;
+            S->out_pack = 0ull;
+            open_job(S, kJobRelax, (uint32_t)((edges + T - 1) / T));
+            return;
+        }
+        if (cnt > 0 && !(err & (kErrCapacity | kErrBounds))) atomicOr(&S->error, kErrIterCap);
+        if (st.kind == 1 && (err & kErrSaturated)) {
+            open_job(S, kJobCheck, (uint32_t)((g.n + kInitChunk - 1) / kInitChunk));
+            return;
+        }
+        complete_query(P, S, slot_status(S));
+        return;
+    }
+    complete_query(P, S, slot_status(S));  // kJobCheck
+}
+
+// ---- tile bodies (block-wide) ------------------------------------------------
+
+__device__ void init_tile(const Params &P, Slot *S, int64_t k) {
+    const SlotState st = slot_state(S);
+    const GraphDev g = P.graphs[st.graph];
+    const int64_t v0 = k * kInitChunk;
+    const int64_t v1 = min(v0 + kInitChunk, g.n);
+    const int32_t src = st.src;
+    const bool sssp = st.kind == 1;
+    const bool reset_epoch = st.epoch_reset != 0;
+    uint32_t *status = st.status;
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
+        status[i] = i == src ? 0u : kInf;
+        if (sssp && reset_epoch) S->epoch[i] = 0u;
+    }
+    if (!sssp) {
+        const int64_t w0 = v0 / 32, w1 = (v1 + 31) / 32;
+        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+            S->bitmap[w] = w == (src >> 5) ? (1u << (src & 31)) : 0u;
+    }
+}
+
+__device__ void check_tile(const Params &P, Slot *S, int64_t k) {
+    const SlotState st = slot_state(S);
+    const GraphDev g = P.graphs[st.graph];
+    const int64_t v0 = k * kInitChunk;
+    const int64_t v1 = min(v0 + kInitChunk, g.n);
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x)
+        if (__ldcg(st.status + i) == kSat) atomicOr(&S->error, kErrOverflow);
+}
+
+template <bool SSSP>
+__device__ void relax_tile(const Params &P, Slot *S, int64_t t, WarpBuf &wb, WarpScratch &ws) {
+    const SlotState st = slot_state(S);
+    const GraphDev g = P.graphs[st.graph];
+    const uint32_t par = st.par;
+    const int64_t in_cnt = st.in_cnt;
+    const int64_t E = (int64_t)st.in_edges;
+    const uint32_t level = st.level;
+    const uint32_t stamp = st.epoch_base + level;
+    uint32_t *status = st.status;
+    const NodeList in = S->lists[par];
+    FlushOut o;
+    o.list = S->lists[par ^ 1u];
+    o.elist = nullptr;
+    o.pack = &S->out_pack;
+    o.cap = P.slot_cap;
+    o.tile_cap = P.tile_cap;
+    o.tile = P.tile;
+    o.mdt = 1;
+    o.err = &S->error;
+    o.pushes = &S->pushes;
+    const int64_t T = P.tile;
+    const int64_t ntiles = (E + T - 1) / T;
+    const int64_t e0 = t * T;
+    const int64_t e1 = min(e0 + T, E);
+    int64_t i0 = __ldcg(in.tstart + t);
+    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldcg(in.tstart + t + 1) + 1, in_cnt) : in_cnt;
+    if (i0 < 0 || i0 >= ihi) {
+        if (threadIdx.x == 0) atomicOr(&S->error, kErrBounds);
+        return;
+    }
+    uint32_t cnt = 0;
+    for (int64_t r0 = e0; r0 < e1; r0 += (int64_t)kBlock * kItems) {
+        int32_t vv[kItems];
+        uint32_t ww[kItems], dd[kItems];
+        bool ok[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const int64_t e = r0 + (int64_t)it * kBlock + threadIdx.x;
+            ok[it] = false;
+            vv[it] = 0;
+            ww[it] = 0;
+            dd[it] = 0;
+            if (e < e1) {
+                const int64_t k = list_search_cg(in.scan, i0, ihi, e);
+                const int64_t eidx = __ldcg(in.beg + k) + (e - __ldcg(in.scan + k));
+                if ((uint64_t)eidx >= (uint64_t)g.m) {
+                    atomicOr(&S->error, kErrBounds);
+                } else {
+                    ok[it] = true;
+                    vv[it] = __ldg(g.col + eidx);
+                    if (SSSP) {
+                        ww[it] = __ldg(g.w + eidx);
+                        const int32_t u = __ldcg(in.v + k);
+                        dd[it] = __ldcg(S->epoch + u) == stamp ? kInf : __ldcg(status + u);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            bool want = false;
+            int64_t vb = 0;
+            uint32_t vd = 0;
+            if (ok[it]) {
+                const bool hit = SSSP ? sssp_relax_cg(status, S->epoch, vv[it], dd[it], ww[it], stamp, &S->error)
+                                      : bfs_claim_cg(S->bitmap, status, vv[it], level + 1);
+                if (hit) {
+                    vb = __ldg(g.off + vv[it]);
+                    vd = (uint32_t)(__ldg(g.off + vv[it] + 1) - vb);
+                    want = vd > 0;
+                }
+            }
+            wpush(wb, cnt, want, vv[it], vb, vd);
+            if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o);
+        }
+    }
+    wflush<kOutNode, true>(wb, ws, cnt, o);
+}
+
+// ---- admission -------------------------------------------------------------
+
+__device__ void admit(const Params &P) {
+    Shared *sh = P.sh;
+    const unsigned long long sub = ld_acquire_sys(&P.host->submitted);
+    unsigned long long con = sh->consumed;
+    int32_t cursor = 0;
+    while (con < sub) {
+        Slot *S = nullptr;
+        for (; cursor < P.nslots; ++cursor)
+            if (((volatile Slot *)&P.slots[cursor])->busy == 0) {
+                S = &P.slots[cursor];
+                break;
+            }
+        if (!S) break;
+        const Req r = P.host->req[con % kRing];
+        S->ticket = r.ticket;
+        S->graph = r.graph;
+        S->src = r.src;
+        S->kind = r.kind;
+        S->status = reinterpret_cast<uint32_t *>(r.out);
+        S->error = 0;
+        S->t_admit = global_ns();
+        S->level = 0;
+        S->relaxed = 0ull;
+        S->pushes = 0ull;
+        S->out_pack = 0ull;
+        bool valid = r.graph >= 0 && r.graph < P.ngraphs && r.out != 0ull && (r.kind == 0 || r.kind == 1);
+        if (valid) {
+            const GraphDev g = P.graphs[r.graph];
+            valid = r.src >= 0 && (int64_t)r.src < g.n && g.n <= P.slot_n && (r.kind == 0 || g.w != nullptr);
+        }
+        if (S->epoch_next == 0u || S->epoch_next > 0xF0000000u) {
+            S->epoch_reset = 1;
+            S->epoch_base = 1;
+        } else {
+            S->epoch_reset = 0;
+            S->epoch_base = S->epoch_next;
+        }
+        S->busy = 1;
+        atomicAdd(&sh->active, 1u);
+        ++con;
+        if (!valid) {
+            complete_query(P, S, LB_ERR_ARG);
+            continue;
+        }
+        const GraphDev g = P.graphs[r.graph];
+        open_job(S, kJobInit, (uint32_t)((g.n + kInitChunk - 1) / kInitChunk));
+    }
+    sh->consumed = con;
+    st_release_sys(&P.host->consumed, con);
+}
+
+// ---- the persistent kernel -------------------------------------------------
+
+__global__ void __launch_bounds__(kBlock) k_serve(Params P) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    __shared__ int s_slot;
+    __shared__ uint32_t s_kind, s_tiles;
+    __shared__ long long s_tile;
+    __shared__ int s_exit;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint64_t idle_since = 0;
+    uint32_t scan_from = blockIdx.x % (uint32_t)P.nslots;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_slot = -1;
+            s_exit = 0;
+            for (int32_t c = 0; c < P.nslots; ++c) {
+                const int32_t si = (int32_t)((scan_from + (uint32_t)c) % (uint32_t)P.nslots);
+                Slot *S = &P.slots[si];
+                const unsigned long long w = __ldcg(&S->claim);
+                const uint32_t kind = __ldcg(&S->job_kind);
+                const uint32_t tiles = __ldcg(&S->job_tiles);
+                if (kind == kJobNone || (uint32_t)w >= tiles) continue;
+                const unsigned long long old = atomicAdd(&S->claim, 1ull);
+                __threadfence();
+                // the claim counts only if the job fields still belong to the
+                // generation it was taken in (a late claim on a finished job
+                // must not take a tile of the slot's next job)
+                const uint32_t g2 = __ldcg(&S->job_gen);
+                const uint32_t k2 = __ldcg(&S->job_kind);
+                const uint32_t t2 = __ldcg(&S->job_tiles);
+                if (g2 == (uint32_t)(old >> 32) && k2 != kJobNone && (uint32_t)old < t2) {
+                    s_slot = si;
+                    s_kind = k2;
+                    s_tiles = t2;
+                    s_tile = (long long)(uint32_t)old;
+                    scan_from = (uint32_t)si;
+                    break;
+                }
+            }
+            if (s_slot < 0) {
+                const uint64_t now = global_ns();
+                // Admission and the decision to stop are taken under one lock,
+                // so no request is admitted after the grid decided to leave.
+                if (atomicCAS(&P.sh->admit_lock, 0u, 1u) == 0u) {
+                    if (__ldcg(&P.sh->stopping) == 0u) {
+                        const unsigned long long before = P.sh->consumed;
+                        admit(P);
+                        const bool admitted = P.sh->consumed != before;
+                        if (admitted || __ldcg(&P.sh->active) != 0u) {
+                            idle_since = 0;
+                        } else if (idle_since == 0) {
+                            idle_since = now;
+                        } else if (now - idle_since > P.idle_ns) {
+                            atomicExch(&P.sh->stopping, 1u);
+                        }
+                    }
+                    __threadfence();
+                    atomicExch(&P.sh->admit_lock, 0u);
+                }
+                if (ld_acquire_sys32(&P.host->stop) != 0u || __ldcg(&P.sh->stopping) != 0u) s_exit = 1;
+                if (now - __ldcg(&P.sh->kernel_t0) > P.hard_ns) {
+                    atomicOr(&P.sh->error, kErrDeadline);
+                    s_exit = 1;
+                }
+                if (!s_exit) __nanosleep(256);
+            } else {
+                idle_since = 0;
+            }
+        }
+        __syncthreads();
+        if (s_exit) break;
+        const int si = s_slot;
+        if (si < 0) continue;
+        Slot *S = &P.slots[si];
+        const uint32_t kind = s_kind;
+        if (kind == kJobInit) init_tile(P, S, s_tile);
+        else if (kind == kJobCheck) check_tile(P, S, s_tile);
+        else if (((const volatile Slot *)S)->kind == 1) relax_tile<true>(P, S, s_tile, s_wb[warp], s_ws[warp]);
+        else relax_tile<false>(P, S, s_tile, s_wb[warp], s_ws[warp]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const uint32_t d = atomicAdd(&S->job_done, 1u);
+            if (d == s_tiles - 1) {
+                __threadfence();
+                finish_job(P, S, kind);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_serve_t0(Shared *sh) {
+    sh->kernel_t0 = global_ns();
+    sh->stopping = 0;
+    sh->admit_lock = 0;
+}
+
+}  // namespace srv
+}  // namespace lbk
+
+// =========================================================================
+// host side
+// =========================================================================
+
+using namespace lbk;
+using namespace lbk::srv;
+
+struct lb_server {
+    int device = 0;
+    int sms = 0;
+    std::mutex mu;
+    lb_server_options opt{};
+    std::vector<lb_graph *> graphs;
+    std::vector<int64_t> graph_n;
+    std::vector<bool> graph_weighted;
+    GraphDev *d_graphs = nullptr;
+    Slot *d_slots = nullptr;
+    Shared *d_shared = nullptr;
+    HostShared *h_ring = nullptr;  // pinned, mapped
+    HostShared *d_ring = nullptr;  // device view
+    std::vector<void *> bufs;      // slot workspace allocations
+    int32_t nslots = 0;
+    int64_t slot_n = 0, slot_m = 0, slot_cap = 0, tile_cap = 0;
+    int64_t slot_bytes = 0;
+    int grid = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_kernel = nullptr;
+    bool launched = false;
+    unsigned long long submitted = 0;  // host copy
+    unsigned long long acked = 0;      // completions handed to the caller
+    unsigned long long next_ticket = 1;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+lb_status sfail(lb_status s, const char *msg, cudaError_t e = cudaSuccess) {
+    char buf[384];
+    if (e != cudaSuccess) snprintf(buf, sizeof(buf), "%s: %s", msg, cudaGetErrorString(e));
+    else snprintf(buf, sizeof(buf), "%s", msg);
+    set_last_error(buf);
+    return s;
+}
+
+#define SV_CU(call, what)                                                    \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess)                                               \
+            return sfail(e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, what, e_); \
+    } while (0)
+
+void destroy_server(lb_server *s) {
+    if (!s) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    if (s->h_ring) {
+        __atomic_store_n(&s->h_ring->stop, 1u, __ATOMIC_RELEASE);
+    }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (void *p : s->bufs) cudaFree(p);
+    if (s->d_graphs) cudaFree(s->d_graphs);
+    if (s->d_slots) cudaFree(s->d_slots);
+    if (s->d_shared) cudaFree(s->d_shared);
+    if (s->h_ring) cudaFreeHost(s->h_ring);
+    if (s->ev_kernel) cudaEventDestroy(s->ev_kernel);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete s;
+}
+
+bool kernel_running(lb_server *s) {
+    if (!s->launched) return false;
+    const cudaError_t q = cudaEventQuery(s->ev_kernel);
+    if (q == cudaErrorNotReady) return true;
+    s->launched = false;
+    return false;
+}
+
+lb_status launch_kernel(lb_server *s) {
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.slots = s->d_slots;
+    P.nslots = s->nslots;
+    P.ngraphs = (int32_t)s->graphs.size();
+    P.graphs = s->d_graphs;
+    P.host = s->d_ring;
+    P.sh = s->d_shared;
+    P.tile = s->opt.tile;
+    P.slot_cap = s->slot_cap;
+    P.tile_cap = s->tile_cap;
+    P.slot_n = s->slot_n;
+    P.idle_ns = (uint64_t)s->opt.idle_us * 1000ull;
+    P.hard_ns = 600ull * 1000000000ull;  // a persistent launch never outlives 10 minutes
+    k_serve_t0<<<1, 1, 0, s->stream>>>(s->d_shared);
+    SV_CU(cudaGetLastError(), "k_serve_t0 launch");
+    k_serve<<<s->grid, kBlock, 0, s->stream>>>(P);
+    SV_CU(cudaGetLastError(), "persistent kernel launch");
+    SV_CU(cudaEventRecord(s->ev_kernel, s->stream), "cudaEventRecord");
+    s->launched = true;
+    s->launches++;
+    return LB_OK;
+}
+
+lb_status ensure_running(lb_server *s) {
+    const unsigned long long consumed = __atomic_load_n(&s->h_ring->consumed, __ATOMIC_ACQUIRE);
+    const bool pending = consumed < s->submitted;
+    const bool inflight = consumed > s->acked || pending;
+    if (!inflight) return LB_OK;
+    if (kernel_running(s)) return LB_OK;
+    // the kernel has left (idle timeout) while work is pending or in flight
+    unsigned int err = 0;
+    SV_CU(cudaMemcpy(&err, &s->d_shared->error, sizeof(err), cudaMemcpyDeviceToHost), "reading kernel status");
+    if (err & kErrDeadline) return sfail(LB_ERR_TIMEOUT, "persistent kernel reached its time limit");
+    return launch_kernel(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_server_options *opt, lb_server **out) {
+    if (!out) return sfail(LB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!graphs || ngraphs < 1 || ngraphs > 4096) return sfail(LB_ERR_ARG, "need 1..4096 graphs");
+    lb_server *s = new (std::nothrow) lb_server();
+    if (!s) return sfail(LB_ERR_OOM, "host allocation failed");
+    lb_server_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.tile == 0) o.tile = 2048;
+    if (o.idle_us == 0) o.idle_us = 1000;
+    if (o.mem_fraction <= 0.0) o.mem_fraction = 0.5;
+    if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > 4096 || o.idle_us < 0 ||
+        o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32) {
+        delete s;
+        return sfail(LB_ERR_ARG, "bad server options");
+    }
+    s->opt = o;
+    lb_status st = LB_OK;
+    cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    std::vector<GraphDev> gd;
+    for (int32_t i = 0; i < ngraphs; ++i) {
+        lb_graph *g = graphs[i];
+        if (!g) { delete s; return sfail(LB_ERR_ARG, "graph handle is NULL"); }
+        int64_t n = 0, m = 0;
+        int32_t wgt = 0, dev = -1;
+        lb_graph_info(g, &n, &m, &wgt, &dev);
+        if (dev != s->device) { delete s; return sfail(LB_ERR_ARG, "every graph must live on the current device"); }
+        GraphDev d;
+        graph_device_arrays(g, &d.off, &d.col, &d.w);
+        d.n = n;
+        d.m = m;
+        gd.push_back(d);
+        s->graphs.push_back(g);
+        s->graph_n.push_back(n);
+        s->graph_weighted.push_back(wgt != 0);
+        if (n > s->slot_n) s->slot_n = n;
+        if (m > s->slot_m) s->slot_m = m;
+    }
+    s->slot_cap = s->slot_n;
+    s->tile_cap = s->slot_m / o.tile + 2;
+    // per slot: bitmap + stamps + two worklists (v, beg, scan, tile starts)
+    const int64_t per_list = 4 * s->slot_cap + 8 * s->slot_cap + 8 * (s->slot_cap + 1) + 4 * s->tile_cap;
+    s->slot_bytes = 4 * ((s->slot_n + 31) / 32) + 4 * s->slot_n + 2 * per_list + 4096;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    int64_t fit = (int64_t)((double)free_b * o.mem_fraction) / (s->slot_bytes > 0 ? s->slot_bytes : 1);
+    int32_t want = o.slots > 0 ? o.slots : 256;
+    if (fit < want) want = (int32_t)fit;
+    if (want < 1) {
+        destroy_server(s);
+        return sfail(LB_ERR_OOM, "not enough free device memory for one query slot");
+    }
+    s->nslots = want;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, kBlock, 0);
+    if (occ < 1) occ = 1;
+    if (o.ctas_per_sm > 0 && o.ctas_per_sm < occ) occ = o.ctas_per_sm;
+    s->grid = occ * s->sms;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_ring, sizeof(HostShared), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        memset(s->h_ring, 0, sizeof(HostShared));
+        e = cudaHostGetDevicePointer((void **)&s->d_ring, s->h_ring, 0);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_graphs, sizeof(GraphDev) * gd.size());
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_graphs, gd.data(), sizeof(GraphDev) * gd.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_shared, sizeof(Shared));
+    if (e == cudaSuccess) e = cudaMemset(s->d_shared, 0, sizeof(Shared));
+    std::vector<Slot> hs((size_t)s->nslots);
+    for (int32_t i = 0; i < s->nslots && e == cudaSuccess; ++i) {
+        Slot &S = hs[(size_t)i];
+        memset(&S, 0, sizeof(Slot));
+        auto get = [&](void **p, size_t bytes) {
+            if (e != cudaSuccess) return;
+            e = cudaMalloc(p, bytes);
+            if (e == cudaSuccess) s->bufs.push_back(*p);
+        };
+        get((void **)&S.bitmap, 4 * (size_t)((s->slot_n + 31) / 32));
+        get((void **)&S.epoch, 4 * (size_t)s->slot_n);
+        if (e == cudaSuccess) e = cudaMemset(S.epoch, 0, 4 * (size_t)s->slot_n);
+        for (int b = 0; b < 2; ++b) {
+            get((void **)&S.lists[b].v, 4 * (size_t)s->slot_cap);
+            get((void **)&S.lists[b].beg, 8 * (size_t)s->slot_cap);
+            get((void **)&S.lists[b].scan, 8 * (size_t)(s->slot_cap + 1));
+            get((void **)&S.lists[b].tstart, 4 * (size_t)s->tile_cap);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_slots, sizeof(Slot) * (size_t)s->nslots);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_slots, hs.data(), sizeof(Slot) * (size_t)s->nslots, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        st = sfail(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "server set-up", e);
+        destroy_server(s);
+        return st;
+    }
+    *out = s;
+    return LB_OK;
+}
+
+lb_status lb_server_destroy(lb_server *s) {
+    destroy_server(s);
+    return LB_OK;
+}
+
+lb_status lb_server_info(const lb_server *s, lb_server_info_t *info) {
+    if (!s || !info) return sfail(LB_ERR_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->slots = s->nslots;
+    info->grid = s->grid;
+    info->slot_bytes = s->slot_bytes;
+    info->slot_n = s->slot_n;
+    info->kernel_launches = (int64_t)s->launches;
+    info->submitted = (int64_t)s->submitted;
+    info->completed = (int64_t)s->acked;
+    return LB_OK;
+}
+
+lb_status lb_server_submit(lb_server *s, int32_t graph, int32_t src, int32_t kind, void *out_dev, uint64_t *ticket) {
+    if (!s || !out_dev) return sfail(LB_ERR_ARG, "NULL argument");
+    if (graph < 0 || graph >= (int32_t)s->graphs.size()) return sfail(LB_ERR_ARG, "graph index out of range");
+    if (src < 0 || (int64_t)src >= s->graph_n[(size_t)graph]) return sfail(LB_ERR_ARG, "source out of range");
+    if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP) return sfail(LB_ERR_ARG, "kind must be LB_KIND_BFS or LB_KIND_SSSP");
+    if (kind == LB_KIND_SSSP && !s->graph_weighted[(size_t)graph]) return sfail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->submitted - s->acked >= kRing) return sfail(LB_ERR_UNSUPPORTED, "request ring full: poll completions first");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    Req &r = s->h_ring->req[s->submitted % kRing];
+    r.graph = graph;
+    r.src = src;
+    r.kind = kind;
+    r.out = (unsigned long long)(uintptr_t)out_dev;
+    r.ticket = s->next_ticket++;
+    if (ticket) *ticket = r.ticket;
+    s->submitted++;
+    __atomic_store_n(&s->h_ring->submitted, s->submitted, __ATOMIC_RELEASE);
+    lb_status st = ensure_running(s);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    return st;
+}
+
+lb_status lb_server_poll(lb_server *s, lb_completion *out, int32_t cap, int32_t *ndone) {
+    if (!s || !ndone || (cap > 0 && !out)) return sfail(LB_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    int32_t k = 0;
+    while (k < cap) {
+        Done &d = s->h_ring->done[s->acked % kRing];
+        const unsigned long long seq = __atomic_load_n(&d.seq, __ATOMIC_ACQUIRE);
+        if (seq != s->acked + 1ull) break;
+        out[k].ticket = d.ticket;
+        out[k].status = d.status;
+        out[k].graph = d.graph;
+        out[k].iterations = d.iterations;
+        out[k].edges_relaxed = (int64_t)d.edges_relaxed;
+        out[k].device_ns = (int64_t)(d.t_done_ns - d.t_admit_ns);
+        ++k;
+        s->acked++;
+    }
+    *ndone = k;
+    lb_status st = ensure_running(s);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    return st;
+}
+
+lb_status lb_server_stop(lb_server *s) {
+    if (!s) return sfail(LB_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    __atomic_store_n(&s->h_ring->stop, 1u, __ATOMIC_RELEASE);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    s->launched = false;
+    __atomic_store_n(&s->h_ring->stop, 0u, __ATOMIC_RELEASE);
+    return LB_OK;
+}
+
+}  // extern "C"

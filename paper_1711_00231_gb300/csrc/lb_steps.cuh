@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
     o.tile_cap = p.tile_cap;
     o.tile = p.tile;
     o.mdt = p.mdt;
+    o.err = &ctl->error;
+    o.pushes = &ctl->pushes;
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     WarpBuf &wb = s_wb[warp];
     WarpScratch &ws = s_ws[warp];
@@ -78,10 +80,10 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
                 ++cur;
             }
             wpush(wb, cnt, want, v, vb, vd);
-            if (cnt > kWB - 32) wflush<OUTK, false>(wb, ws, cnt, o, ctl);
+            if (cnt > kWB - 32) wflush<OUTK, false>(wb, ws, cnt, o);
         }
     }
-    wflush<OUTK, false>(wb, ws, cnt, o, ctl);
+    wflush<OUTK, false>(wb, ws, cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }
 
@@ -173,7 +175,7 @@ __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const No
                     }
                 }
                 wpush(wb, cnt, want, vv[it], vb, vd);
-                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o, ctl);
+                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o);
             }
         }
     }
@@ -199,10 +201,12 @@ __global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams
     o.tile_cap = p.tile_cap;
     o.tile = p.tile;
     o.mdt = p.mdt;
+    o.err = &ctl->error;
+    o.pushes = &ctl->pushes;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
     wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
-    wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o, ctl);
+    wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }
 
@@ -231,6 +235,8 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
     o.tile_cap = 0;
     o.tile = p.tile;
     o.mdt = p.mdt;
+    o.err = &ctl->error;
+    o.pushes = &ctl->pushes;
     const uint32_t warp = threadIdx.x >> 5;
     WarpBuf &wb = s_wb[warp];
     WarpScratch &ws = s_ws[warp];
@@ -276,10 +282,10 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
                 }
             }
             wpush(wb, cnt, want, vv[it], vb, vd);
-            if (cnt > kWB - 32) wflush<kOutEdges, false>(wb, ws, cnt, o, ctl);
+            if (cnt > kWB - 32) wflush<kOutEdges, false>(wb, ws, cnt, o);
         }
     }
-    wflush<kOutEdges, false>(wb, ws, cnt, o, ctl);
+    wflush<kOutEdges, false>(wb, ws, cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, false, p.elist_cap);
 }
 
@@ -360,6 +366,8 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     osup.tile_cap = p.tile_cap;
     osup.tile = p.tile;
     osup.mdt = p.mdt;
+    osup.err = &ctl->error;
+    osup.pushes = &ctl->pushes;
     FlushOut osub = osup;
     osub.list = p.subs[from == kHpFromSuper ? 0u : (sub_in ^ 1u)];
     osub.pack = &ctl->sub_pack;
@@ -396,7 +404,7 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
             const bool keep = rest > 0 && (!SSSP || du != kInf);
             if (SSSP && du == kInf) end = cur;
             wpush(sb, scnt, keep, u, end, (uint32_t)rest);
-            if (scnt > kWB - 32) wflush<kOutNode, true>(sb, ws, scnt, osub, ctl);
+            if (scnt > kWB - 32) wflush<kOutNode, true>(sb, ws, scnt, osub);
             while (__any_sync(kFull, cur < end)) {
                 bool want = false;
                 int32_t v = 0;
@@ -414,12 +422,12 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
                     ++cur;
                 }
                 wpush(wb, cnt, want, v, vb, vd);
-                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, osup, ctl);
+                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, osup);
             }
         }
     }
-    wflush<kOutNode, true>(wb, ws, cnt, osup, ctl);
-    wflush<kOutNode, true>(sb, ws, scnt, osub, ctl);
+    wflush<kOutNode, true>(wb, ws, cnt, osup);
+    wflush<kOutNode, true>(sb, ws, scnt, osub);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_hp_step(p, ctl);
 }
 

@@ -347,14 +347,16 @@ __global__ void k_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList 
     o.tile_cap = T + 1;
     o.tile = (int32_t)ept;
     o.mdt = 1;
+    o.err = &ctl->error;
+    o.pushes = &ctl->pushes;
     uint32_t cnt = 0;
     for (int64_t c = 0; c < F; c += 32) {
         const int64_t i = c + lane;
         const bool want = i < F;
         wpush(wb, cnt, want, want ? (int32_t)i : 0, 0, want ? (uint32_t)deg[i] : 0u);
-        if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o, ctl);
+        if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o);
     }
-    wflush<kOutNode, true>(wb, ws, cnt, o, ctl);
+    wflush<kOutNode, true>(wb, ws, cnt, o);
     if (lane == 0) list.scan[F] = E;
 }
 

@@ -57,6 +57,25 @@ class lb_query_stats(ctypes.Structure):
         return {k: (float(getattr(self, k)) if k == "device_ms" else int(getattr(self, k))) for k, _ in self._fields_}
 
 
+class lb_server_options(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("idle_us", ctypes.c_int32), ("mem_fraction", ctypes.c_double), ("reserved", ctypes.c_int32 * 8)]
+
+
+class lb_server_info_t(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("grid", ctypes.c_int32), ("slot_bytes", ctypes.c_int64),
+                ("slot_n", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("submitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class lb_completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("iterations", ctypes.c_int64), ("edges_relaxed", ctypes.c_int64), ("device_ns", ctypes.c_int64)]
+
+
 class lb_step_record(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("list_size", ctypes.c_int64),
                 ("edges", ctypes.c_int64)]
@@ -93,6 +112,13 @@ def _load():
         "lb_wd_offsets": ([P, i64, i64, P, P, P], st),
         "lb_set_allocator": ([P, P, P], st),
         "lb_bfs_wd_noalloc": ([P, P, i64, i64, i32, P, P], st),
+        "lb_autotune": ([P, i32, st, P, i32, ctypes.POINTER(lb_options), ctypes.POINTER(ctypes.c_double)], st),
+        "lb_server_create": ([P, i32, ctypes.POINTER(lb_server_options), ctypes.POINTER(P)], st),
+        "lb_server_destroy": ([P], st),
+        "lb_server_info": ([P, ctypes.POINTER(lb_server_info_t)], st),
+        "lb_server_submit": ([P, i32, i32, i32, P, ctypes.POINTER(ctypes.c_uint64)], st),
+        "lb_server_poll": ([P, P, i32, ctypes.POINTER(i32)], st),
+        "lb_server_stop": ([P], st),
         "lb_last_error": ([], ctypes.c_char_p),
         "lb_version": ([], ctypes.c_char_p),
     }
@@ -244,6 +270,16 @@ def lb_release_workspaces(g: int) -> None:
     _check(_load().lb_release_workspaces(g))
 
 
+def lb_autotune(g: int, kind: int, strategy, srcs):
+    """Picks the fastest options for (kind, strategy) on these sources and
+    keeps them on the graph; returns (options dict, mean ms per query)."""
+    a = np.ascontiguousarray(srcs, dtype=np.int32)
+    o = lb_options()
+    ms = ctypes.c_double()
+    _check(_load().lb_autotune(g, kind, _strategy(strategy), _ptr(a), a.size, ctypes.byref(o), ctypes.byref(ms)))
+    return {k: int(getattr(o, k)) for k, _ in o._fields_ if k != "reserved"}, float(ms.value)
+
+
 def lb_mdt(g: int, bins: int = 10):
     mdt, md, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
     _check(_load().lb_mdt(g, bins, ctypes.byref(mdt), ctypes.byref(md), ctypes.byref(b)))
@@ -266,6 +302,52 @@ def lb_bfs_wd_noalloc(offsets_dev, cols_dev, n: int, m: int, src: int, levels_de
     the library; n <= 131072, m <= 16777216."""
     _check(_load().lb_bfs_wd_noalloc(_ptr(offsets_dev), _ptr(cols_dev), n, m, src, _ptr(levels_dev),
                                      _stream_handle(stream)))
+
+
+def lb_server_create(graphs, slots: int = 0, ctas_per_sm: int = 0, tile: int = 0, idle_us: int = 0,
+                     mem_fraction: float = 0.0) -> int:
+    """Persistent multi-query engine over resident graphs (lb_graph handles)."""
+    arr = (ctypes.c_void_p * len(graphs))(*graphs)
+    o = lb_server_options(slots=slots, ctas_per_sm=ctas_per_sm, tile=tile, idle_us=idle_us, mem_fraction=mem_fraction)
+    h = ctypes.c_void_p()
+    _check(_load().lb_server_create(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def lb_server_destroy(s: int) -> None:
+    _check(_load().lb_server_destroy(s))
+
+
+def lb_server_info(s: int) -> dict:
+    i = lb_server_info_t()
+    _check(_load().lb_server_info(s, ctypes.byref(i)))
+    return i.as_dict()
+
+
+def lb_server_submit(s: int, graph: int, src: int, kind: int, out_dev) -> int:
+    t = ctypes.c_uint64()
+    _check(_load().lb_server_submit(s, graph, src, kind, _ptr(out_dev), ctypes.byref(t)))
+    return int(t.value)
+
+
+_POLL_CAP = 4096
+_poll_buf = None
+
+
+def lb_server_poll(s: int, cap: int = _POLL_CAP):
+    """List of completion dicts (ticket, status, graph, iterations,
+    edges_relaxed, device_ns)."""
+    global _poll_buf
+    if _poll_buf is None or len(_poll_buf) < cap:
+        _poll_buf = (lb_completion * cap)()
+    n = ctypes.c_int32()
+    _check(_load().lb_server_poll(s, ctypes.cast(_poll_buf, ctypes.c_void_p), cap, ctypes.byref(n)))
+    return [(int(c.ticket), int(c.status), int(c.graph), int(c.iterations), int(c.edges_relaxed), int(c.device_ns))
+            for c in _poll_buf[:n.value]]
+
+
+def lb_server_stop(s: int) -> None:
+    _check(_load().lb_server_stop(s))
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -370,6 +452,9 @@ class Graph:
 
     def mdt(self, bins: int = 10):
         return lb_mdt(self.h, bins)
+
+    def autotune(self, kind: str, strategy, srcs):
+        return lb_autotune(self.h, LB_KIND_BFS if kind == "bfs" else LB_KIND_SSSP, strategy, srcs)
 
     def release(self):
         lb_release_workspaces(self.h)

@@ -1,0 +1,140 @@
+"""Batched / served queries through the persistent multi-query engine
+(lb_server_*): every result must equal the oracle's bit for bit, alone and
+in a mix, whatever the arrival pattern, slot count or tile size."""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from paper_1711_00231_gb300 import lb
+from paper_1711_00231_gb300 import serve as sv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1711_00231_gb300 import _build
+    _build.build()
+
+
+@pytest.fixture(scope="module")
+def mix():
+    graphs = [gg.rmat(12, 8, seed=1), gg.rmat(14, 16, seed=2), gg.grid(64, 48, seed=3),
+              gg.erdos_renyi(3000, 12000, seed=4), gg.rmat(13, 32, seed=5, weights=None),
+              gg.from_edges(6, [0, 1, 2], [1, 2, 3], [1, 2, 3])]
+    handles = [lb.Graph.from_csr(g) for g in graphs]
+    yield graphs, handles
+    for h in handles:
+        h.close()
+
+
+def reference(g, kind, src):
+    if kind == "bfs":
+        return oracle.bfs(g, src)[0]
+    return oracle.dijkstra(g, src)[0].view(np.int32)
+
+
+def make_requests(graphs, n, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n):
+        gi = int(rng.integers(0, len(graphs)))
+        kind = "sssp" if graphs[gi].weights is not None and rng.random() < 0.5 else "bfs"
+        reqs.append(sv.Request(0.0, gi, int(rng.integers(0, graphs[gi].n)), kind))
+    return reqs
+
+
+@pytest.mark.parametrize("slots,tile", [(0, 0), (3, 256), (17, 8192)])
+def test_batch_matches_oracle(mix, slots, tile):
+    import torch
+    graphs, handles = mix
+    reqs = make_requests(graphs, 60, seed=slots + tile)
+    outs = [torch.full((graphs[r.graph].n,), 7, dtype=torch.int32, device="cuda") for r in reqs]
+    S = sv.Server(handles, slots=slots, tile=tile)
+    try:
+        st = S.run_batch(reqs, outs, timeout_s=120)
+        assert all(x == 0 for x in st), st
+        torch.cuda.synchronize()
+        for r, o in zip(reqs, outs):
+            assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src)), r
+        info = S.info()
+        assert info["completed"] == len(reqs) and info["slots"] >= 1
+        if slots:
+            assert info["slots"] == slots
+    finally:
+        S.close()
+
+
+def test_same_result_alone_and_in_the_mix(mix):
+    import torch
+    graphs, handles = mix
+    S = sv.Server(handles, slots=8)
+    try:
+        probe = sv.Request(0.0, 1, 77, "sssp")
+        alone = torch.empty(graphs[1].n, dtype=torch.int32, device="cuda")
+        assert S.run_batch([probe], [alone]) == [0]
+        reqs = make_requests(graphs, 40, seed=9)
+        reqs.insert(17, probe)
+        outs = [torch.empty(graphs[r.graph].n, dtype=torch.int32, device="cuda") for r in reqs]
+        assert all(x == 0 for x in S.run_batch(reqs, outs))
+        torch.cuda.synchronize()
+        assert torch.equal(outs[17], alone)
+        # and equal to the single-query entry point
+        single = torch.empty_like(alone)
+        handles[1].sssp_dev(77, "WD", single)
+        torch.cuda.synchronize()
+        assert torch.equal(single, alone)
+    finally:
+        S.close()
+
+
+def test_continuous_arrivals_and_relaunch(mix):
+    import torch
+    graphs, handles = mix
+    S = sv.Server(handles, slots=4, idle_us=200)
+    try:
+        reqs = make_requests(graphs, 30, seed=11)
+        for i, r in enumerate(reqs):
+            r.arrival_s = 0.002 * i
+        outs = [torch.empty(graphs[r.graph].n, dtype=torch.int32, device="cuda") for r in reqs]
+        res = sv.serve(S, reqs, outs, timeout_s=120)
+        assert res["statuses_ok"] and res["queries"] == 30
+        torch.cuda.synchronize()
+        for r, o in zip(reqs, outs):
+            assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src))
+        time.sleep(0.05)      # longer than idle_us: the persistent kernel leaves
+        more = make_requests(graphs, 5, seed=12)
+        outs2 = [torch.empty(graphs[r.graph].n, dtype=torch.int32, device="cuda") for r in more]
+        assert all(x == 0 for x in S.run_batch(more, outs2))
+        torch.cuda.synchronize()
+        for r, o in zip(more, outs2):
+            assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src))
+        assert S.info()["kernel_launches"] >= 2
+    finally:
+        S.close()
+
+
+def test_overflow_and_invalid_requests(mix):
+    import torch
+    graphs, handles = mix
+    big = 0x80000000
+    g = gg.from_edges(4, [0, 1, 2], [1, 2, 3], [big, big - 3, 5])
+    G = lb.Graph.from_csr(g)
+    S = sv.Server([G, handles[4]], slots=2)
+    try:
+        out = torch.empty(4, dtype=torch.int32, device="cuda")
+        st = S.run_batch([sv.Request(0.0, 0, 0, "sssp")], [out])
+        assert st == [lb.LB_ERR_OVERFLOW]
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.dijkstra(g, 0)[0])
+        with pytest.raises(lb.LbError):
+            S.submit(0, 9, "bfs", out)            # source out of range
+        with pytest.raises(lb.LbError):
+            S.submit(1, 0, "sssp", out)           # unweighted graph
+        with pytest.raises(lb.LbError):
+            S.submit(5, 0, "bfs", out)            # no such graph
+    finally:
+        S.close()
+        G.close()
