@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--loop-mode", type=int, default=0,
                     help="0: device-resident loop (CUDA graph WHILE); 1: host loop (for per-kernel profiling)")
     ap.add_argument("--kinds", default="bfs,sssp")
+    ap.add_argument("--no-serve", action="store_true", help="skip the batched-serving measurement")
+    ap.add_argument("--serve-queries", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -203,6 +205,112 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def chunking_ablation(torch, sources: int = 4):
+    """The paper's Sec. IV-D experiment on an rmat20-shaped graph (R-MAT
+    scale 20, edge factor 16): EP with work chunking (one reservation for all
+    edges of the nodes a warp updated) against EP with one atomic per pushed
+    edge."""
+    import graphgen as gg
+    from paper_1711_00231_gb300 import lb
+    g = gg.rmat(20, 16, seed=1)
+    G = lb.Graph.from_csr(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    srcs = gg.pick_sources(g, sources, seed=1)
+    row = {}
+    for kind in ("bfs", "sssp"):
+        for s_name in ("EP", "EP_NOCHUNK"):
+            tot = 0.0
+            for s in srcs:
+                for rep in range(2):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    (G.bfs_dev if kind == "bfs" else G.sssp_dev)(int(s), s_name, out)
+                    b.record()
+                    torch.cuda.synchronize()
+                    if rep == 1:
+                        tot += a.elapsed_time(b)
+            row[f"{kind}_{s_name}_ms"] = tot / len(srcs)
+        row[f"{kind}_chunking_speedup"] = row[f"{kind}_EP_NOCHUNK_ms"] / row[f"{kind}_EP_ms"]
+    G.close()
+    row["graph"] = "R-MAT scale 20, edge factor 16, seed 1 (paper: 1.11-3.125x, mean 1.82x on its graphs)"
+    return row
+
+
+def serving_mix(seed: int = 1):
+    """The resident graph mix of the serving workload: 24 R-MAT graphs
+    (scale 12..20, edge factor 8/16/32, drawn with `seed`) and 8 grids
+    (256^2 .. 2048^2, two weight seeds each), all with weights U[1,255]."""
+    import graphgen as gg
+    rng = np.random.default_rng(seed)
+    scales = rng.integers(12, 21, 24)
+    efs = rng.choice([8, 16, 32], 24)
+    graphs = [gg.rmat(int(sc), int(ef), seed=100 + i) for i, (sc, ef) in enumerate(zip(scales, efs))]
+    for i, side in enumerate([256, 512, 1024, 2048]):
+        for ws in (1, 2):
+            graphs.append(gg.grid(side, side, seed=200 + 2 * i + ws, weights=(1, 255)))
+    return graphs
+
+
+def serving_bench(args, torch):
+    """Batched serving vs one query at a time on the same GPU: 1,024 queries
+    (BFS / SSSP 50/50, graph uniform, source uniform over out-degree > 0)
+    over 32 resident graphs.  Reports queries/s with every query available at
+    once, and p50 / p99 arrival-to-result latency under Poisson arrivals at
+    0.8x the one-at-a-time capacity; checks every batched result against the
+    one-at-a-time result bit for bit."""
+    import graphgen as gg
+    from paper_1711_00231_gb300 import lb
+    from paper_1711_00231_gb300 import serve as sv
+    t0 = time.time()
+    cg = serving_mix(1)
+    t_gen = time.time() - t0
+    G = [lb.Graph.from_csr(g) for g in cg]
+    cand = [np.flatnonzero(g.degrees() > 0).astype(np.int32) for g in cg]
+    burst = sv.poisson_schedule(args.serve_queries, float("inf"), [g.n for g in cg], cand, seed=1)
+    outs_a = [torch.empty(cg[r.graph].n, dtype=torch.int32, device="cuda") for r in burst]
+    outs_b = [torch.empty(cg[r.graph].n, dtype=torch.int32, device="cuda") for r in burst]
+    # one at a time: warm every graph's loop, then the whole burst back to back
+    for gi, g in enumerate(G):
+        tmp = torch.empty(cg[gi].n, dtype=torch.int32, device="cuda")
+        g.bfs_dev(int(cand[gi][0]), "WD", tmp)
+        g.sssp_dev(int(cand[gi][0]), "WD", tmp)
+    torch.cuda.synchronize()
+    one = sv.serve_one_at_a_time(G, burst, outs_a)
+    S = sv.Server(G)
+    info = S.info()
+    S.run_batch(burst[:64], outs_b[:64])     # warm the persistent kernel
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st = S.run_batch(burst, outs_b)
+    torch.cuda.synchronize()
+    batched_s = time.perf_counter() - t1
+    exact = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b)) and all(x == 0 for x in st)
+    rate = 0.8 * one["qps"]
+    pois = sv.poisson_schedule(args.serve_queries, rate, [g.n for g in cg], cand, seed=1)
+    one_p = sv.serve_one_at_a_time(G, pois, outs_a)
+    srv_p = sv.serve(S, pois, outs_b)
+    torch.cuda.synchronize()
+    exact_p = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b)) and srv_p["statuses_ok"]
+    rate_hi = 0.8 * args.serve_queries / batched_s
+    pois_hi = sv.poisson_schedule(args.serve_queries, rate_hi, [g.n for g in cg], cand, seed=2)
+    srv_hi = sv.serve(S, pois_hi, outs_b)
+    info2 = S.info()
+    S.close()
+    for g in G:
+        g.close()
+    return {"workload": "32 graphs (24 R-MAT scale 12-20 ef 8/16/32, 8 grids 256^2-2048^2), weights U[1,255]; "
+                        f"{args.serve_queries} queries, BFS/SSSP 50/50, seed 1",
+            "one_at_a_time_qps": one["qps"], "batched_qps": args.serve_queries / batched_s,
+            "speedup_qps": (args.serve_queries / batched_s) / one["qps"],
+            "poisson_rate_qps": rate,
+            "one_at_a_time_latency": {k: one_p[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
+            "batched_latency": {k: srv_p[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
+            "batched_latency_at_0.8x_batched_capacity": {"rate_qps": rate_hi, **{k: srv_hi[k] for k in
+                                                                                 ("p50_ms", "p99_ms", "qps")}},
+            "exact_vs_one_at_a_time": bool(exact and exact_p), "slots": info["slots"], "grid": info["grid"],
+            "kernel_launches": info2["kernel_launches"], "generate_s": t_gen}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -248,6 +356,7 @@ def main():
 
     # work per query (edges and vertices reached), from a first run
     work = {}
+    trace_first = {}
     for kind in kinds:
         for s in srcs:
             query(kind, s)
@@ -256,6 +365,15 @@ def main():
             if st["status"] != 0:
                 raise SystemExit(f"query failed: {kind} src={s} status={st['status']}")
             work[(kind, int(s))] = m_reached_torch(out, deg_t) + (st["steps"], st["iterations"], st["edges_relaxed"])
+            if int(s) == int(srcs[0]):
+                tr = G.trace()
+                prev = 0
+                steps_first = []
+                for rec in tr:
+                    steps_first.append({"level": int(rec["level"]), "list": int(rec["list_size"]),
+                                        "edges": int(rec["edges"]), "us": round((int(rec["t_ns"]) - prev) / 1e3, 1)})
+                    prev = int(rec["t_ns"])
+                trace_first[kind] = steps_first
     ev = {k: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
           for k in kinds}
 
@@ -353,6 +471,7 @@ def main():
             row["speedup_wd_vs_ep"] = row["EP"]["ms_per_query"] / row["WD"]["ms_per_query"]
             extra[kind] = row
         G.release()
+        extra["chunking_ablation"] = chunking_ablation(torch)
 
     # end to end through the host-buffer C-ABI calls (lb_bfs / lb_sssp):
     # includes the D2H copy of every result into pinned host memory
@@ -376,6 +495,10 @@ def main():
                "note": "graph resident; per query the source id goes in as a launch argument and the n x 4 B "
                        "result comes back to pinned host memory"}
 
+    batched = None
+    if rank == 0 and not args.no_serve:
+        batched = serving_bench(args, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(g, srcs[:2], args.cpu_seconds)
@@ -389,7 +512,8 @@ def main():
                                loop="device (CUDA graph WHILE)" if args.loop_mode == 0 else "host"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": sum(res[k]["launches"] for k in kinds),
-                "per_kind": res, "strategies": extra,
+                "per_kind": res, "strategies": extra, "batched": batched,
+                "steps_of_first_query": trace_first,
                 "setup_s": {"generate": t_gen, "upload": t_upload}, "elapsed_ms_timed_region": elapsed_ms}
         print(json.dumps(line), flush=True)
     G.close()

@@ -54,6 +54,9 @@ typedef enum lb_strategy {
     LB_HP = 4,  /* hierarchical processing: sub-iterations that relax at most
                    MDT edges per node, switching to WD below a list-size
                    threshold (Sec. III-C) */
+    LB_EP_NOCHUNK = 6, /* EP without work chunking: one atomic reservation per
+                   pushed edge, the default the paper's Sec. IV-D compares
+                   work chunking against */
     LB_AUTO = 15 /* the library's choice (currently LB_WD) */
 } lb_strategy;
 
@@ -128,6 +131,8 @@ typedef struct lb_step_record {
     int32_t mode;          /* 0 relax, 1 HP sub-iteration, 2 HP WD step */
     int64_t list_size;     /* entries in the list this step consumed */
     int64_t edges;         /* edges relaxed by this step */
+    int64_t t_ns;          /* device time at the end of the step, in ns from
+                              the start of the query (the set-up kernel) */
 } lb_step_record;
 
 /* ------------------------------------------------------------ graphs --- */

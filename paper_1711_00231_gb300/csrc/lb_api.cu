@@ -77,7 +77,9 @@ struct DeviceGuard {
     }
 };
 
-constexpr int kStrategies = 5;
+constexpr int kStrategies = 7;
+
+bool is_ep(int s) { return s == LB_EP || s == LB_EP_NOCHUNK; }
 
 int64_t round_tiles(int64_t m, int64_t tile) { return m / tile + 2; }
 
@@ -280,7 +282,7 @@ lb_status ensure_workspace(lb_graph *g, int s) {
         LB_CU(cudaMemsetAsync(g->epoch, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
     }
     if (s == LB_NS || s == LB_HP) LB_TRY(ensure_mdt(g));
-    if (s == LB_EP) {
+    if (is_ep(s)) {
         if (!g->coo_src) {
             LB_TRY(g->alloc(&g->coo_src, g->m));
             GraphDev gd{g->off, g->col, g->w, g->n, g->m};
@@ -414,7 +416,7 @@ lb_status run_query(lb_graph *g, int kind, int s, int32_t src, void *out_dev, in
     if (!g) return fail(LB_ERR_ARG, "graph is NULL");
     if (src < 0 || (int64_t)src >= g->n) return fail(LB_ERR_ARG, "source %d out of range [0, %lld)", src, (long long)g->n);
     if (s == LB_AUTO) s = LB_WD;
-    if (s < 0 || s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy %d", s);
+    if (s < 0 || s >= kStrategies || s == 5) return fail(LB_ERR_ARG, "unknown strategy %d", s);
     if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
     if (!out_dev) return fail(LB_ERR_ARG, "output buffer is NULL");
     if (parents_dev && kind == LB_KIND_SSSP && g->zero_weight)
@@ -730,7 +732,7 @@ lb_status lb_last_trace(lb_graph *g, lb_step_record *out, int64_t cap, int64_t *
 lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
     if (!g || !out) return fail(LB_ERR_ARG, "NULL argument");
     if (s == LB_AUTO) s = LB_WD;
-    if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy %d", (int)s);
+    if ((int)s < 0 || (int)s >= kStrategies || (int)s == 5) return fail(LB_ERR_ARG, "unknown strategy %d", (int)s);
     std::lock_guard<std::mutex> lk(g->mu);
     DeviceGuard dg(g->device);
     memset(out, 0, sizeof(*out));
@@ -747,7 +749,7 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
         out->mdt = g->mdt;
         out->ns_children = g->ns_children;
     }
-    if (s == LB_EP) {
+    if (is_ep(s)) {
         out->coo_src = 4 * (m > 0 ? m : 1);
         out->edge_lists = 2 * 4 * (m > 0 ? m : 1);
     } else {
@@ -779,7 +781,7 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
     if (!g || !srcs || nsrc < 1 || nsrc > 1024) return fail(LB_ERR_ARG, "need a graph and 1..1024 sources");
     if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP) return fail(LB_ERR_ARG, "bad kind");
     if (s == LB_AUTO) s = LB_WD;
-    if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy");
+    if ((int)s < 0 || (int)s >= kStrategies || (int)s == 5) return fail(LB_ERR_ARG, "unknown strategy");
     for (int32_t i = 0; i < nsrc; ++i)
         if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return fail(LB_ERR_ARG, "source out of range");
     if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
@@ -800,7 +802,7 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
                     o.hp_threshold = h;
                     cands.push_back(o);
                 }
-            } else if (s == LB_WD || s == LB_EP || c == 0 || t == 2048) {
+            } else if (s == LB_WD || is_ep(s) || c == 0 || t == 2048) {
                 lb_options o = base;
                 o.wd_tile = t;
                 o.ctas_per_sm = c;

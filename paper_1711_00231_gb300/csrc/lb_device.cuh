@@ -28,7 +28,7 @@ constexpr int kWB = 128;  // entries per warp push buffer (multiple of 32)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // what a flush writes
-enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2 };
+enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2, kOutEdgesPerEdge = 3 };
 
 struct WarpBuf {
     int64_t beg[kWB];
@@ -193,6 +193,97 @@ __device__ __forceinline__ uint32_t sssp_source_dist(const uint32_t *__restrict_
     return epoch[u] == stamp ? kInf : status[u];
 }
 
+// Relaxes ITEMS loaded edges of a warp and pushes the vertices that must be
+// queued.  The relax runs in stages over all items -- plain checks, then
+// every atomic, then every offset load of a won vertex, then the pushes --
+// so the latencies of the items overlap instead of queueing behind one
+// another (a warp-synchronous push between items would serialise them).
+template <bool SSSP, int ITEMS, int KIND, bool TILED>
+__device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32_t (&vv)[ITEMS],
+                                            const uint32_t (&ww)[ITEMS], const uint32_t (&dd)[ITEMS],
+                                            const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
+                                            uint32_t *__restrict__ epoch, uint32_t *__restrict__ status,
+                                            uint32_t level, uint32_t stamp, uint32_t *err, WarpBuf &wb,
+                                            WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    bool cand[ITEMS];
+    uint32_t val[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        cand[it] = false;
+        val[it] = 0;
+        if (!ok[it]) continue;
+        if (SSSP) {
+            if (dd[it] == kInf) continue;
+            const uint64_t a64 = (uint64_t)dd[it] + (uint64_t)ww[it];
+            val[it] = a64 >= kSat ? kSat : (uint32_t)a64;
+            cand[it] = val[it] < status[vv[it]];
+        } else {
+            cand[it] = !(bitmap[(uint32_t)vv[it] >> 5] & (1u << ((uint32_t)vv[it] & 31u)));
+        }
+    }
+    uint32_t prev[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        prev[it] = 0;
+        if (!cand[it]) continue;
+        if (SSSP) prev[it] = atomicMin(&status[vv[it]], val[it]);
+        else prev[it] = atomicOr(&bitmap[(uint32_t)vv[it] >> 5], 1u << ((uint32_t)vv[it] & 31u));
+    }
+    bool won[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        if (SSSP) {
+            won[it] = cand[it] && val[it] < prev[it];
+            if (won[it] && val[it] == kSat) atomicOr(err, kErrSaturated);
+        } else {
+            won[it] = cand[it] && !(prev[it] & (1u << ((uint32_t)vv[it] & 31u)));
+            if (won[it]) status[vv[it]] = level + 1;
+        }
+    }
+    if (SSSP) {
+        // queue only the first improvement of v in this iteration
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it)
+            if (won[it] && epoch[vv[it]] == stamp) won[it] = false;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it)
+            if (won[it]) prev[it] = atomicExch(&epoch[vv[it]], stamp);
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it)
+            if (won[it] && prev[it] == stamp) won[it] = false;
+    }
+    int64_t vb[ITEMS], ve[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        vb[it] = 0;
+        ve[it] = 0;
+        if (won[it]) {
+            vb[it] = __ldg(off + vv[it]);
+            ve[it] = __ldg(off + vv[it] + 1);
+        }
+    }
+    if (KIND == kOutEdgesPerEdge) {
+        // no work chunking: one reservation per pushed edge id
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            if (!won[it]) continue;
+            for (int64_t e = vb[it]; e < ve[it]; ++e) {
+                const unsigned long long pos = atomicAdd(o.pack, (1ull << 32) | 1ull) >> 32;
+                if ((int64_t)pos < o.cap) o.elist[pos] = (int32_t)e;
+                else atomicOr(o.err, kErrCapacity);
+            }
+            atomicAdd(o.pushes, (unsigned long long)(ve[it] - vb[it]));
+        }
+        return;
+    }
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const bool want = won[it] && ve[it] > vb[it];
+        wpush(wb, cnt, want, vv[it], vb[it], (uint32_t)(ve[it] - vb[it]));
+        if (cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
+    }
+}
+
 // ---- end-of-step protocol ----------------------------------------------------
 
 __device__ __forceinline__ bool block_is_last(Ctl *ctl) {
@@ -211,6 +302,14 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *(const volatile unsigned long long *)p;
 }
 
+
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ void trace_append(Ctl *ctl, int32_t mode, int64_t list_size, int64_t edges) {
     const uint32_t t = ctl->trace_len;
     if (t < (uint32_t)kTraceMax) {
@@ -218,14 +317,9 @@ __device__ __forceinline__ void trace_append(Ctl *ctl, int32_t mode, int64_t lis
         ctl->trace[t].mode = mode;
         ctl->trace[t].list_size = list_size;
         ctl->trace[t].edges = edges;
+        ctl->trace[t].t_ns = (int64_t)(global_ns() - ctl->t_start);
         ctl->trace_len = t + 1;
     }
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
 }
 
 __device__ __forceinline__ void set_loop(const StepParams &p, Ctl *ctl, bool more) {

@@ -48,6 +48,7 @@ struct TraceRec {
     int32_t mode;
     int64_t list_size;
     int64_t edges;
+    int64_t t_ns;  // device time at the end of the step, from the query's start
 };
 
 struct Ctl {
@@ -76,6 +77,7 @@ struct Ctl {
     uint64_t max_steps;
     uint64_t step;
     uint64_t t_deadline;  // %globaltimer (ns) after which the loop stops
+    uint64_t t_start;     // %globaltimer (ns) when the query was prepared
     unsigned long long relaxed;
     unsigned long long pushes;
     uint32_t trace_len;

@@ -7,7 +7,7 @@
 namespace lbk {
 
 #ifndef LB_WD_ITEMS
-#define LB_WD_ITEMS 4
+#define LB_WD_ITEMS 2
 #endif
 #ifndef LB_EP_ITEMS
 #define LB_EP_ITEMS 4
@@ -19,8 +19,8 @@ cudaError_t launch_step_entry(bool sssp, bool granules, const StepParams &p, int
 int occupancy_step_entry(bool sssp, bool granules);
 cudaError_t launch_step_wd(bool sssp, const StepParams &p, int grid, cudaStream_t st);
 int occupancy_step_wd(bool sssp);
-cudaError_t launch_step_ep(bool sssp, const StepParams &p, int grid, cudaStream_t st);
-int occupancy_step_ep(bool sssp);
+cudaError_t launch_step_ep(bool sssp, bool chunk, const StepParams &p, int grid, cudaStream_t st);
+int occupancy_step_ep(bool sssp, bool chunk);
 cudaError_t launch_step_hp(bool sssp, const StepParams &p, int grid, cudaStream_t st);
 int occupancy_step_hp(bool sssp);
 

@@ -9,7 +9,7 @@
 #include "lb_device.cuh"
 
 #ifndef LB_WD_MIN_BLOCKS
-#define LB_WD_MIN_BLOCKS 1
+#define LB_WD_MIN_BLOCKS 6
 #endif
 #ifndef LB_WD_WARP_LOOKUP
 #define LB_WD_WARP_LOOKUP 0
@@ -160,23 +160,8 @@ __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const No
                     }
                 }
             }
-#pragma unroll
-            for (int it = 0; it < ITEMS; ++it) {
-                bool want = false;
-                int64_t vb = 0;
-                uint32_t vd = 0;
-                if (ok[it]) {
-                    const bool hit = SSSP ? sssp_relax(status, p.epoch, vv[it], dd[it], ww[it], stamp, ctl)
-                                          : bfs_claim(p.bitmap, status, vv[it], level + 1);
-                    if (hit) {
-                        vb = __ldg(p.g.off + vv[it]);
-                        vd = (uint32_t)(__ldg(p.g.off + vv[it] + 1) - vb);
-                        want = vd > 0;
-                    }
-                }
-                wpush(wb, cnt, want, vv[it], vb, vd);
-                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o);
-            }
+            relax_items<SSSP, ITEMS, kOutNode, true>(ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status, level, stamp,
+                                                     &ctl->error, wb, ws, cnt, o);
         }
     }
 }
@@ -216,7 +201,7 @@ __global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams
 // arrays, which double as the COO dst / wt arrays).  An updated node pushes
 // all of its edge ids with one reservation (work chunking).
 // ---------------------------------------------------------------------------
-template <bool SSSP, int ITEMS>
+template <bool SSSP, int ITEMS, bool CHUNK>
 __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
@@ -267,23 +252,8 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
                 }
             }
         }
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-            bool want = false;
-            int64_t vb = 0;
-            uint32_t vd = 0;
-            if (ok[it]) {
-                const bool hit = SSSP ? sssp_relax(status, p.epoch, vv[it], dd[it], ww[it], stamp, ctl)
-                                      : bfs_claim(p.bitmap, status, vv[it], level + 1);
-                if (hit) {
-                    vb = __ldg(p.g.off + vv[it]);
-                    vd = (uint32_t)(__ldg(p.g.off + vv[it] + 1) - vb);
-                    want = vd > 0;
-                }
-            }
-            wpush(wb, cnt, want, vv[it], vb, vd);
-            if (cnt > kWB - 32) wflush<kOutEdges, false>(wb, ws, cnt, o);
-        }
+        relax_items<SSSP, ITEMS, CHUNK ? kOutEdges : kOutEdgesPerEdge, false>(
+            ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status, level, stamp, &ctl->error, wb, ws, cnt, o);
     }
     wflush<kOutEdges, false>(wb, ws, cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, false, p.elist_cap);

@@ -14,7 +14,8 @@ cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, 
         case LB_BS: return launch_step_entry(sssp, false, p, grid, st);
         case LB_NS: return launch_step_entry(sssp, true, p, grid, st);
         case LB_WD: return launch_step_wd(sssp, p, grid, st);
-        case LB_EP: return launch_step_ep(sssp, p, grid, st);
+        case LB_EP: return launch_step_ep(sssp, true, p, grid, st);
+        case LB_EP_NOCHUNK: return launch_step_ep(sssp, false, p, grid, st);
         case LB_HP: return launch_step_hp(sssp, p, grid, st);
         default: return cudaErrorInvalidValue;
     }
@@ -25,7 +26,8 @@ int step_blocks_per_sm(int strategy, bool sssp) {
         case LB_BS: return occupancy_step_entry(sssp, false);
         case LB_NS: return occupancy_step_entry(sssp, true);
         case LB_WD: return occupancy_step_wd(sssp);
-        case LB_EP: return occupancy_step_ep(sssp);
+        case LB_EP: return occupancy_step_ep(sssp, true);
+        case LB_EP_NOCHUNK: return occupancy_step_ep(sssp, false);
         case LB_HP: return occupancy_step_hp(sssp);
         default: return 1;
     }
@@ -37,7 +39,7 @@ int step_blocks_per_sm(int strategy, bool sssp) {
 // edges) for the strategy's list kind.
 __device__ __forceinline__ int64_t source_units(int strategy, int64_t deg, int32_t mdt) {
     if (deg == 0) return 0;
-    if (strategy == LB_EP) return deg;
+    if (strategy == LB_EP || strategy == LB_EP_NOCHUNK) return deg;
     if (strategy == LB_NS) return deg <= mdt ? 1 : (deg + mdt - 1) / mdt;
     return 1;
 }
@@ -72,7 +74,8 @@ __global__ void k_prepare(StepParams p, int32_t src, uint32_t *status, int kind,
     }
     c->max_levels = max_levels;
     c->max_steps = max_steps;
-    c->t_deadline = global_ns() + time_limit_ns;
+    c->t_start = global_ns();
+    c->t_deadline = c->t_start + time_limit_ns;
     c->step = 0;
     c->relaxed = 0ull;
     c->pushes = 0ull;
@@ -99,7 +102,7 @@ __global__ void k_init(StepParams p) {
     }
     const int64_t beg = p.g.off[src];
     const int64_t deg = p.g.off[src + 1] - beg;
-    if (p.strategy == LB_EP) {
+    if (p.strategy == LB_EP || p.strategy == LB_EP_NOCHUNK) {
         for (int64_t j = tid; j < deg; j += stride) p.elist[0][j] = (int32_t)(beg + j);
         return;
     }

@@ -17,8 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblb.so")
 
 # lb_strategy
-LB_BS, LB_EP, LB_WD, LB_NS, LB_HP, LB_AUTO = 0, 1, 2, 3, 4, 15
-STRATEGIES = {"BS": LB_BS, "EP": LB_EP, "WD": LB_WD, "NS": LB_NS, "HP": LB_HP, "AUTO": LB_AUTO}
+LB_BS, LB_EP, LB_WD, LB_NS, LB_HP, LB_EP_NOCHUNK, LB_AUTO = 0, 1, 2, 3, 4, 6, 15
+STRATEGIES = {"BS": LB_BS, "EP": LB_EP, "WD": LB_WD, "NS": LB_NS, "HP": LB_HP, "EP_NOCHUNK": LB_EP_NOCHUNK,
+              "AUTO": LB_AUTO}
 # lb_status
 LB_OK, LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_OVERFLOW = 0, -1, -2, -3, -4
 LB_ERR_TIMEOUT, LB_ERR_UNSUPPORTED, LB_ERR_INTERNAL = -5, -6, -7
@@ -78,7 +79,7 @@ class lb_completion(ctypes.Structure):
 
 class lb_step_record(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("list_size", ctypes.c_int64),
-                ("edges", ctypes.c_int64)]
+                ("edges", ctypes.c_int64), ("t_ns", ctypes.c_int64)]
 
 
 _lib = None
@@ -256,8 +257,9 @@ def lb_last_trace(g: int, cap: int = 4096) -> np.ndarray:
     ln = ctypes.c_int64()
     _check(_load().lb_last_trace(g, ctypes.cast(buf, ctypes.c_void_p), cap, ctypes.byref(ln)))
     k = min(ln.value, cap)
-    return np.array([(buf[i].level, buf[i].mode, buf[i].list_size, buf[i].edges) for i in range(k)],
-                    dtype=[("level", np.int32), ("mode", np.int32), ("list_size", np.int64), ("edges", np.int64)])
+    return np.array([(buf[i].level, buf[i].mode, buf[i].list_size, buf[i].edges, buf[i].t_ns) for i in range(k)],
+                    dtype=[("level", np.int32), ("mode", np.int32), ("list_size", np.int64), ("edges", np.int64),
+                           ("t_ns", np.int64)])
 
 
 def lb_mem_report(g: int, strategy) -> dict:

@@ -11,7 +11,7 @@ from paper_1711_00231_gb300 import lb
 
 pytestmark = pytest.mark.gpu
 
-STRATS = ["BS", "EP", "WD", "NS", "HP"]
+STRATS = ["BS", "EP", "WD", "NS", "HP", "EP_NOCHUNK"]
 
 
 @pytest.fixture(scope="module", autouse=True)
