@@ -54,6 +54,10 @@ typedef enum lb_strategy {
     LB_HP = 4,  /* hierarchical processing: sub-iterations that relax at most
                    MDT edges per node, switching to WD below a list-size
                    threshold (Sec. III-C) */
+    LB_NS_PHYS = 5, /* node splitting with physical child nodes: ids n..n+S-1,
+                   child lists, distances mirrored from the parent with
+                   extra atomics, as in the paper's NS algorithm; same
+                   results as LB_NS, more memory and atomics */
     LB_EP_NOCHUNK = 6, /* EP without work chunking: one atomic reservation per
                    pushed edge, the default the paper's Sec. IV-D compares
                    work chunking against */
@@ -111,6 +115,8 @@ typedef struct lb_mem_stats {
     int64_t resident;      /* bytes this graph holds on the device now */
     int64_t ns_children;   /* NS: child nodes created at the current MDT */
     int64_t mdt;           /* the MDT NS/HP use (0 if not yet computed) */
+    int64_t ns_split;      /* NS_PHYS: child map, parent map and child
+                              distances (4n + 8S); counted in extra_total */
 } lb_mem_stats;
 
 /* Per-query counters of the last query on a graph (lb_last_stats). */

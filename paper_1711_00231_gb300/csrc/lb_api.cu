@@ -117,6 +117,12 @@ struct lb_graph {
     int32_t *elist[2]{};
     int64_t elist_cap = 0;
     int32_t *coo_src = nullptr;
+    int32_t *child_first = nullptr;         // NS_PHYS split map (n)
+    int32_t *parent_of = nullptr;           // NS_PHYS (children)
+    uint32_t *child_dist = nullptr;         // NS_PHYS (children)
+    unsigned long long *ns_sums = nullptr;  // NS_PHYS build scratch (n / 1024 + 1)
+    int64_t phys_mdt = -1;                  // MDT the split map was built for
+    int64_t phys_children = 0;
     unsigned long long *scratch = nullptr;  // MDT histogram / counters (4097 words)
     int64_t *dres = nullptr;                // device results (4 words)
     int64_t *hres = nullptr;                // pinned host mirror
@@ -235,6 +241,12 @@ void free_workspace(lb_graph *g) {
     for (int b = 0; b < 2; ++b) g->release(g->elist[b], g->elist_cap);
     g->elist_cap = 0;
     g->release(g->coo_src, g->m);
+    g->release(g->child_first, g->n);
+    g->release(g->parent_of, g->phys_children);
+    g->release(g->child_dist, g->phys_children);
+    g->release(g->ns_sums, g->n / 1024 + 1);
+    g->phys_mdt = -1;
+    g->phys_children = 0;
 }
 
 // MDT with the graph's options (histogram on the device, cached).
@@ -268,7 +280,7 @@ lb_status ensure_mdt(lb_graph *g) {
 }
 
 int64_t node_list_cap(const lb_graph *g, int s) {
-    return s == LB_NS ? g->n + (g->ns_children > 0 ? g->ns_children : 0) : g->n;
+    return (s == LB_NS || s == LB_NS_PHYS) ? g->n + (g->ns_children > 0 ? g->ns_children : 0) : g->n;
 }
 
 // Allocates what strategy s needs; any reallocation invalidates the cached
@@ -281,7 +293,22 @@ lb_status ensure_workspace(lb_graph *g, int s) {
         LB_TRY(g->alloc(&g->epoch, g->n));
         LB_CU(cudaMemsetAsync(g->epoch, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
     }
-    if (s == LB_NS || s == LB_HP) LB_TRY(ensure_mdt(g));
+    if (s == LB_NS || s == LB_NS_PHYS || s == LB_HP) LB_TRY(ensure_mdt(g));
+    if (s == LB_NS_PHYS && g->phys_mdt != g->mdt) {
+        quiesce(g);
+        drop_execs(g);
+        g->release(g->child_first, g->n);
+        g->release(g->parent_of, g->phys_children);
+        g->release(g->child_dist, g->phys_children);
+        g->phys_children = g->ns_children;
+        LB_TRY(g->alloc(&g->child_first, g->n));
+        LB_TRY(g->alloc(&g->parent_of, g->phys_children));
+        LB_TRY(g->alloc(&g->child_dist, g->phys_children));
+        if (!g->ns_sums) LB_TRY(g->alloc(&g->ns_sums, g->n / 1024 + 1));
+        GraphDev gd{g->off, g->col, g->w, g->n, g->m};
+        LB_CU(launch_ns_phys_build(gd, (int32_t)g->mdt, g->child_first, g->parent_of, g->ns_sums, g->stream));
+        g->phys_mdt = g->mdt;
+    }
     if (is_ep(s)) {
         if (!g->coo_src) {
             LB_TRY(g->alloc(&g->coo_src, g->m));
@@ -337,6 +364,10 @@ StepParams make_params(const lb_graph *g, int s) {
         p.elist[b] = g->elist[b];
     }
     p.coo_src = g->coo_src;
+    p.child_first = g->child_first;
+    p.parent_of = g->parent_of;
+    p.child_dist = g->child_dist;
+    p.n_children = g->phys_children;
     p.bitmap = g->bitmap;
     p.epoch = g->epoch;
     p.list_cap = s == LB_HP ? (g->list_cap < g->n ? g->list_cap : g->n) : g->list_cap;
@@ -416,7 +447,7 @@ lb_status run_query(lb_graph *g, int kind, int s, int32_t src, void *out_dev, in
     if (!g) return fail(LB_ERR_ARG, "graph is NULL");
     if (src < 0 || (int64_t)src >= g->n) return fail(LB_ERR_ARG, "source %d out of range [0, %lld)", src, (long long)g->n);
     if (s == LB_AUTO) s = LB_WD;
-    if (s < 0 || s >= kStrategies || s == 5) return fail(LB_ERR_ARG, "unknown strategy %d", s);
+    if (s < 0 || s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy %d", s);
     if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
     if (!out_dev) return fail(LB_ERR_ARG, "output buffer is NULL");
     if (parents_dev && kind == LB_KIND_SSSP && g->zero_weight)
@@ -705,7 +736,7 @@ lb_status lb_last_stats(lb_graph *g, lb_query_stats *out) {
     out->steps = (int64_t)h.step;
     out->edges_relaxed = (int64_t)h.relaxed;
     out->pushes = (int64_t)h.pushes;
-    out->mdt = (g->last_strategy == LB_NS || g->last_strategy == LB_HP) ? g->mdt : 0;
+    out->mdt = (g->last_strategy == LB_NS || g->last_strategy == LB_NS_PHYS || g->last_strategy == LB_HP) ? g->mdt : 0;
     out->strategy = g->last_strategy;
     out->device_ms = ms;
     out->status = status_from_error(h.error);
@@ -732,7 +763,7 @@ lb_status lb_last_trace(lb_graph *g, lb_step_record *out, int64_t cap, int64_t *
 lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
     if (!g || !out) return fail(LB_ERR_ARG, "NULL argument");
     if (s == LB_AUTO) s = LB_WD;
-    if ((int)s < 0 || (int)s >= kStrategies || (int)s == 5) return fail(LB_ERR_ARG, "unknown strategy %d", (int)s);
+    if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy %d", (int)s);
     std::lock_guard<std::mutex> lk(g->mu);
     DeviceGuard dg(g->device);
     memset(out, 0, sizeof(*out));
@@ -744,11 +775,12 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
     out->status = 4 * n;
     out->visited = 4 * ((n + 31) / 32) + 4 * n;
     const int64_t tcap = round_tiles(m, g->opt.wd_tile);
-    if (s == LB_NS || s == LB_HP) {
+    if (s == LB_NS || s == LB_NS_PHYS || s == LB_HP) {
         LB_TRY(ensure_mdt(g));
         out->mdt = g->mdt;
         out->ns_children = g->ns_children;
     }
+    if (s == LB_NS_PHYS) out->ns_split = 4 * n + 8 * (out->ns_children > 0 ? out->ns_children : 1);
     if (is_ep(s)) {
         out->coo_src = 4 * (m > 0 ? m : 1);
         out->edge_lists = 2 * 4 * (m > 0 ? m : 1);
@@ -760,7 +792,7 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
     }
     out->control = (int64_t)sizeof(Ctl);
     out->extra_total = out->status + out->visited + out->node_lists + out->tile_starts + out->coo_src +
-                       out->edge_lists + out->sub_lists + out->control;
+                       out->edge_lists + out->sub_lists + out->control + out->ns_split;
     out->resident = g->resident;
     return LB_OK;
 }
@@ -781,7 +813,7 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
     if (!g || !srcs || nsrc < 1 || nsrc > 1024) return fail(LB_ERR_ARG, "need a graph and 1..1024 sources");
     if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP) return fail(LB_ERR_ARG, "bad kind");
     if (s == LB_AUTO) s = LB_WD;
-    if ((int)s < 0 || (int)s >= kStrategies || (int)s == 5) return fail(LB_ERR_ARG, "unknown strategy");
+    if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy");
     for (int32_t i = 0; i < nsrc; ++i)
         if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return fail(LB_ERR_ARG, "source out of range");
     if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");

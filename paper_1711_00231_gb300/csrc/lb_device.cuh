@@ -28,7 +28,7 @@ constexpr int kWB = 128;  // entries per warp push buffer (multiple of 32)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // what a flush writes
-enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2, kOutEdgesPerEdge = 3 };
+enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2, kOutEdgesPerEdge = 3, kOutPhys = 4 };
 
 struct WarpBuf {
     int64_t beg[kWB];
@@ -47,6 +47,7 @@ struct FlushOut {
     unsigned long long *pack;
     uint32_t *err;               // error word (capacity overflow)
     unsigned long long *pushes;  // push counter
+    const int32_t *child_first;  // kOutPhys: first child id of each split node
     int64_t cap;       // entries the output can hold
     int64_t tile_cap;  // tstart entries
     int32_t tile;
@@ -64,7 +65,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 template <int KIND>
 __device__ __forceinline__ uint32_t out_units(uint32_t deg, int32_t mdt) {
     if (KIND == kOutEdges) return deg;
-    if (KIND == kOutGranule) return deg <= (uint32_t)mdt ? 1u : (deg + (uint32_t)mdt - 1u) / (uint32_t)mdt;
+    if (KIND == kOutGranule || KIND == kOutPhys)
+        return deg <= (uint32_t)mdt ? 1u : (deg + (uint32_t)mdt - 1u) / (uint32_t)mdt;
     return 1u;
 }
 
@@ -142,9 +144,10 @@ __device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const F
         for (uint32_t j = lane; j < run_u; j += 32) {
             const uint32_t i = smem_upper(s.pu, cnt, j);
             const int64_t k = (int64_t)(j - s.pu[i]);
-            if (KIND == kOutGranule) {
+            if (KIND == kOutGranule || KIND == kOutPhys) {
                 const int64_t pos = ubase + j;
-                o.list.v[pos] = b.v[i];
+                // a physically split node's runs after the first belong to its children
+                o.list.v[pos] = (KIND == kOutPhys && k > 0) ? __ldg(o.child_first + b.v[i]) + (int32_t)(k - 1) : b.v[i];
                 o.list.beg[pos] = b.beg[i] + k * o.mdt;
                 o.list.scan[pos] = ebase + s.pe[i] + k * o.mdt;
             } else {

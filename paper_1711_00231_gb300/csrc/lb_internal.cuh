@@ -109,6 +109,10 @@ struct StepParams {
     const int32_t *coo_src;
     uint32_t *bitmap;
     uint32_t *epoch;
+    const int32_t *child_first;  // NS_PHYS: first child id of a split node, -1 if not split
+    const int32_t *parent_of;    // NS_PHYS: parent of child n + i
+    uint32_t *child_dist;        // NS_PHYS: mirrored distance of child n + i
+    int64_t n_children;          // NS_PHYS: children created at p.mdt
     int64_t list_cap;
     int64_t tile_cap;
     int64_t elist_cap;
@@ -133,6 +137,8 @@ cudaError_t launch_mdt(const GraphDev &g, int32_t bins, unsigned long long *scra
                        cudaStream_t st);
 cudaError_t launch_validate(const GraphDev &g, uint32_t *err, cudaStream_t st);
 cudaError_t launch_ns_count(const GraphDev &g, int32_t mdt, unsigned long long *out, cudaStream_t st);
+cudaError_t launch_ns_phys_build(const GraphDev &g, int32_t mdt, int32_t *child_first, int32_t *parent_of,
+                                 unsigned long long *block_sums, cudaStream_t st);
 cudaError_t launch_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList list, Ctl *ctl, int64_t *ept_out,
                               cudaStream_t st);
 cudaError_t launch_parents(const StepParams &p, bool sssp, int32_t *parents, cudaStream_t st);

@@ -1,4 +1,4 @@
-// BS (node per thread) and NS (granule per thread) step kernels.
+// BS (node per thread), NS (granule per thread) and physical-NS step kernels.
 #include "lb_launch.h"
 #include "lb_steps.cuh"
 
@@ -20,6 +20,19 @@ cudaError_t launch_step_entry(bool sssp, bool granules, const StepParams &p, int
         else k_step_entry<false, kOutNode><<<grid, kBlock, 0, st>>>(p);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_step_phys(bool sssp, const StepParams &p, int grid, cudaStream_t st) {
+    if (sssp) k_step_phys<true><<<grid, kBlock, 0, st>>>(p);
+    else k_step_phys<false><<<grid, kBlock, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+int occupancy_step_phys(bool sssp) {
+    int nb = 0;
+    cudaError_t e = sssp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_phys<true>, kBlock, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_phys<false>, kBlock, 0);
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 int occupancy_step_entry(bool sssp, bool granules) {

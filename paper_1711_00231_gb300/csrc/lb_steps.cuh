@@ -88,6 +88,109 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Node splitting with physical child nodes (Sec. III-B and its listings): a
+// node of out-degree d > MDT has ceil(d/MDT) - 1 children with ids n..n+S-1,
+// each owning the next run of MDT of its edges; children have no in-edges.
+// The parent's distance is reflected onto its children: whoever lowers a
+// split node's distance also lowers its children's (the extra child-update
+// atomics the paper lists as NS's cost), and an updated node is queued
+// together with its children.  Thread per worklist entry, as in the
+// node-based kernel.
+// ---------------------------------------------------------------------------
+template <bool SSSP>
+__global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const uint32_t par = ctl->par;
+    const int64_t in_cnt = ctl->in_cnt;
+    const uint32_t level = ctl->level;
+    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *status = ctl->status;
+    const int64_t n = p.g.n;
+    const NodeList in = p.lists[par];
+    FlushOut o;
+    o.list = p.lists[par ^ 1u];
+    o.elist = nullptr;
+    o.pack = &ctl->out_pack;
+    o.cap = p.list_cap;
+    o.tile_cap = p.tile_cap;
+    o.tile = p.tile;
+    o.mdt = p.mdt;
+    o.err = &ctl->error;
+    o.pushes = &ctl->pushes;
+    o.child_first = p.child_first;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    WarpBuf &wb = s_wb[warp];
+    WarpScratch &ws = s_ws[warp];
+    uint32_t cnt = 0;
+    const int64_t mdt = p.mdt;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
+        const int64_t i = base + lane;
+        int64_t cur = 0, end = 0;
+        uint32_t du = 0;
+        if (i < in_cnt) {
+            cur = __ldg(in.beg + i);
+            end = cur + (__ldg(in.scan + i + 1) - __ldg(in.scan + i));
+            const int32_t x = __ldg(in.v + i);
+            if (cur < 0 || end > p.g.m || cur > end || x < 0 || (int64_t)x >= n + p.n_children) {
+                atomicOr(&ctl->error, kErrBounds);
+                cur = end = 0;
+            } else if (SSSP) {
+                if ((int64_t)x < n) {
+                    du = sssp_source_dist(status, p.epoch, x, stamp);
+                } else {
+                    const int32_t parent = __ldg(p.parent_of + (x - n));
+                    du = p.epoch[parent] == stamp ? kInf : p.child_dist[x - n];
+                }
+            }
+        }
+        while (__any_sync(kFull, cur < end)) {
+            bool want = false;
+            int32_t v = 0;
+            int64_t vb = 0;
+            uint32_t vd = 0;
+            if (cur < end) {
+                v = __ldg(p.g.col + cur);
+                if (SSSP) {
+                    const uint64_t a64 = (uint64_t)du + (uint64_t)__ldg(p.g.w + cur);
+                    const uint32_t alt = du == kInf ? kInf : (a64 >= kSat ? kSat : (uint32_t)a64);
+                    if (alt < status[v]) {
+                        const uint32_t old = atomicMin(&status[v], alt);
+                        if (alt < old) {
+                            if (alt == kSat) atomicOr(&ctl->error, kErrSaturated);
+                            vb = __ldg(p.g.off + v);
+                            vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
+                            const int32_t cf = __ldg(p.child_first + v);
+                            if (cf >= 0) {
+                                const int64_t nk = ((int64_t)vd + mdt - 1) / mdt - 1;
+                                for (int64_t c = 0; c < nk; ++c) atomicMin(&p.child_dist[cf - n + c], alt);
+                            }
+                            want = vd > 0 && p.epoch[v] != stamp && atomicExch(&p.epoch[v], stamp) != stamp;
+                        }
+                    }
+                } else if (bfs_claim(p.bitmap, status, v, level + 1)) {
+                    vb = __ldg(p.g.off + v);
+                    vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
+                    const int32_t cf = __ldg(p.child_first + v);
+                    if (cf >= 0) {
+                        const int64_t nk = ((int64_t)vd + mdt - 1) / mdt - 1;
+                        for (int64_t c = 0; c < nk; ++c) p.child_dist[cf - n + c] = level + 1;
+                    }
+                    want = vd > 0;
+                }
+                ++cur;
+            }
+            wpush(wb, cnt, want, v, vb, vd);
+            if (cnt > kWB - 32) wflush<kOutPhys, false>(wb, ws, cnt, o);
+        }
+    }
+    wflush<kOutPhys, false>(wb, ws, cnt, o);
+    if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
+}
+
+// ---------------------------------------------------------------------------
 // Workload decomposition over CTA tiles.  The input list's edges (in list
 // order) are cut into tiles of p.tile edges; tile t starts in entry
 // tstart[t] (written by the push that created the list).  Inside a tile,

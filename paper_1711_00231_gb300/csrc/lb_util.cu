@@ -13,6 +13,7 @@ cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, 
     switch (strategy) {
         case LB_BS: return launch_step_entry(sssp, false, p, grid, st);
         case LB_NS: return launch_step_entry(sssp, true, p, grid, st);
+        case LB_NS_PHYS: return launch_step_phys(sssp, p, grid, st);
         case LB_WD: return launch_step_wd(sssp, p, grid, st);
         case LB_EP: return launch_step_ep(sssp, true, p, grid, st);
         case LB_EP_NOCHUNK: return launch_step_ep(sssp, false, p, grid, st);
@@ -25,6 +26,7 @@ int step_blocks_per_sm(int strategy, bool sssp) {
     switch (strategy) {
         case LB_BS: return occupancy_step_entry(sssp, false);
         case LB_NS: return occupancy_step_entry(sssp, true);
+        case LB_NS_PHYS: return occupancy_step_phys(sssp);
         case LB_WD: return occupancy_step_wd(sssp);
         case LB_EP: return occupancy_step_ep(sssp, true);
         case LB_EP_NOCHUNK: return occupancy_step_ep(sssp, false);
@@ -40,7 +42,7 @@ int step_blocks_per_sm(int strategy, bool sssp) {
 __device__ __forceinline__ int64_t source_units(int strategy, int64_t deg, int32_t mdt) {
     if (deg == 0) return 0;
     if (strategy == LB_EP || strategy == LB_EP_NOCHUNK) return deg;
-    if (strategy == LB_NS) return deg <= mdt ? 1 : (deg + mdt - 1) / mdt;
+    if (strategy == LB_NS || strategy == LB_NS_PHYS) return deg <= mdt ? 1 : (deg + mdt - 1) / mdt;
     return 1;
 }
 
@@ -107,10 +109,20 @@ __global__ void k_init(StepParams p) {
         return;
     }
     const NodeList L = p.lists[0];
-    if (p.strategy == LB_NS) {
-        const int64_t units = source_units(LB_NS, deg, p.mdt);
+    if (p.strategy == LB_NS_PHYS) {
+        // every child distance starts unknown; the source's children start at 0
+        const int32_t cf = p.child_first[src];
+        const int64_t nk = deg > p.mdt ? (deg + p.mdt - 1) / p.mdt - 1 : 0;
+        for (int64_t c = tid; c < p.n_children; c += stride) {
+            const int64_t id = n + c;
+            p.child_dist[c] = (cf >= 0 && id >= cf && id < cf + nk) ? 0u : kInf;
+        }
+    }
+    if (p.strategy == LB_NS || p.strategy == LB_NS_PHYS) {
+        const int64_t units = source_units(p.strategy, deg, p.mdt);
+        const int32_t cf = p.strategy == LB_NS_PHYS ? p.child_first[src] : -1;
         for (int64_t j = tid; j < units; j += stride) {
-            L.v[j] = src;
+            L.v[j] = (cf >= 0 && j > 0) ? cf + (int32_t)(j - 1) : src;
             L.beg[j] = beg + j * p.mdt;
             L.scan[j] = j * p.mdt;
         }
@@ -256,6 +268,77 @@ cudaError_t launch_ns_count(const GraphDev &g, int32_t mdt, unsigned long long *
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_ns_count<<<608, kBlock, 0, st>>>(g, mdt, out);
+    return cudaGetLastError();
+}
+
+// Physical node split (Sec. III-B): child ids are handed out in node order.
+// Block b of 1024 nodes first sums its children; a serial scan turns the
+// block sums into offsets; then each block scans its nodes' child counts and
+// writes child_first (n + offset, or -1) and parent_of for every child.
+__device__ __forceinline__ int64_t ns_children_of(const GraphDev &g, int64_t u, int64_t mdt) {
+    const int64_t d = g.off[u + 1] - g.off[u];
+    return d > mdt ? (d + mdt - 1) / mdt - 1 : 0;
+}
+
+__global__ void k_ns_block_sums(GraphDev g, int32_t mdt, unsigned long long *sums) {
+    __shared__ unsigned long long sh[32];
+    const int64_t u = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    unsigned long long k = u < g.n ? (unsigned long long)ns_children_of(g, u, mdt) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(kFull, k, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = k;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < 32; ++i) t += sh[i];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_ns_scan_sums(unsigned long long *sums, int64_t nb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const unsigned long long x = sums[b];
+        sums[b] = run;
+        run += x;
+    }
+}
+
+__global__ void k_ns_assign(GraphDev g, int32_t mdt, const unsigned long long *sums, int32_t *child_first,
+                            int32_t *parent_of) {
+    __shared__ unsigned long long warp_tot[32];
+    const int64_t u = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const unsigned long long k = u < g.n ? (unsigned long long)ns_children_of(g, u, mdt) : 0ull;
+    unsigned long long incl = k;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = warp_tot[lane];
+        unsigned long long wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, wi, o);
+            if ((int)lane >= o) wi += t;
+        }
+        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+    }
+    __syncthreads();
+    if (u >= g.n) return;
+    const int64_t first = (int64_t)(sums[blockIdx.x] + warp_tot[wid] + incl - k);
+    child_first[u] = k > 0 ? (int32_t)(g.n + first) : -1;
+    for (unsigned long long j = 0; j < k; ++j) parent_of[first + (int64_t)j] = (int32_t)u;
+}
+
+cudaError_t launch_ns_phys_build(const GraphDev &g, int32_t mdt, int32_t *child_first, int32_t *parent_of,
+                                 unsigned long long *block_sums, cudaStream_t st) {
+    const int64_t nb = (g.n + 1023) / 1024;
+    k_ns_block_sums<<<(unsigned)nb, 1024, 0, st>>>(g, mdt, block_sums);
+    k_ns_scan_sums<<<1, 32, 0, st>>>(block_sums, nb);
+    k_ns_assign<<<(unsigned)nb, 1024, 0, st>>>(g, mdt, block_sums, child_first, parent_of);
     return cudaGetLastError();
 }
 

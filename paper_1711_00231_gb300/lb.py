@@ -17,9 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblb.so")
 
 # lb_strategy
-LB_BS, LB_EP, LB_WD, LB_NS, LB_HP, LB_EP_NOCHUNK, LB_AUTO = 0, 1, 2, 3, 4, 6, 15
-STRATEGIES = {"BS": LB_BS, "EP": LB_EP, "WD": LB_WD, "NS": LB_NS, "HP": LB_HP, "EP_NOCHUNK": LB_EP_NOCHUNK,
-              "AUTO": LB_AUTO}
+LB_BS, LB_EP, LB_WD, LB_NS, LB_HP, LB_NS_PHYS, LB_EP_NOCHUNK, LB_AUTO = 0, 1, 2, 3, 4, 5, 6, 15
+STRATEGIES = {"BS": LB_BS, "EP": LB_EP, "WD": LB_WD, "NS": LB_NS, "HP": LB_HP, "NS_PHYS": LB_NS_PHYS,
+              "EP_NOCHUNK": LB_EP_NOCHUNK, "AUTO": LB_AUTO}
 # lb_status
 LB_OK, LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_OVERFLOW = 0, -1, -2, -3, -4
 LB_ERR_TIMEOUT, LB_ERR_UNSUPPORTED, LB_ERR_INTERNAL = -5, -6, -7
@@ -43,7 +43,8 @@ class lb_options(ctypes.Structure):
 class lb_mem_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "csr_offsets", "csr_cols", "csr_weights", "status", "visited", "node_lists", "tile_starts", "coo_src",
-        "edge_lists", "sub_lists", "control", "extra_total", "base_total", "resident", "ns_children", "mdt")]
+        "edge_lists", "sub_lists", "control", "extra_total", "base_total", "resident", "ns_children", "mdt",
+        "ns_split")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

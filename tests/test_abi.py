@@ -46,7 +46,7 @@ def test_struct_layouts_match_header(tmp_path):
 #include "lb.h"
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lb_options), sizeof(lb_mem_stats), sizeof(lb_query_stats), sizeof(lb_step_record));
-  printf("%zu %zu %zu %zu\n", offsetof(lb_query_stats, status), offsetof(lb_query_stats, device_ms), offsetof(lb_mem_stats, mdt), offsetof(lb_step_record, t_ns));
+  printf("%zu %zu %zu %zu\n", offsetof(lb_query_stats, status), offsetof(lb_query_stats, device_ms), offsetof(lb_mem_stats, ns_split), offsetof(lb_step_record, t_ns));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -56,7 +56,7 @@ int main(void) {
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(lb.lb_options), ctypes.sizeof(lb.lb_mem_stats), ctypes.sizeof(lb.lb_query_stats),
                      ctypes.sizeof(lb.lb_step_record)]
-    assert offs == [lb.lb_query_stats.status.offset, lb.lb_query_stats.device_ms.offset, lb.lb_mem_stats.mdt.offset,
+    assert offs == [lb.lb_query_stats.status.offset, lb.lb_query_stats.device_ms.offset, lb.lb_mem_stats.ns_split.offset,
                     lb.lb_step_record.t_ns.offset]
 
 

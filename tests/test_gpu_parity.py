@@ -11,7 +11,7 @@ from paper_1711_00231_gb300 import lb
 
 pytestmark = pytest.mark.gpu
 
-STRATS = ["BS", "EP", "WD", "NS", "HP", "EP_NOCHUNK"]
+STRATS = ["BS", "EP", "WD", "NS", "HP", "NS_PHYS", "EP_NOCHUNK"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -310,6 +310,27 @@ def test_ns_granules_match_paper_example():
         assert lvl1["list_size"].tolist() == [sum(runs)] and lvl1["edges"].tolist() == [12]
         rep = G.mem_report("NS")
         assert rep["mdt"] == 4 and rep["ns_children"] == oracle.ns_split(g.offsets, 4)[0] == 2
+    finally:
+        G.close()
+
+
+def test_ns_phys_matches_paper_example_and_reports_memory():
+    # node 8 (7 out-edges) at MDT 4 becomes node 8 and one child 8' holding
+    # the remaining 3 edges; the list of level 1 holds nodes 1, 1', 8, 8'
+    g = _two_node_frontier_graph(5, 7)
+    G = lb.Graph.from_csr(g)
+    try:
+        G.set_options(mdt_override=4)
+        lev = G.bfs(0, "NS_PHYS")
+        assert np.array_equal(lev, oracle.bfs(g, 0)[0])
+        tr = G.trace()
+        lvl1 = tr[tr["level"] == 1]
+        assert lvl1["list_size"].tolist() == [4] and lvl1["edges"].tolist() == [12]
+        rep = G.mem_report("NS_PHYS")
+        children = oracle.ns_split(g.offsets, 4)[0]
+        assert rep["ns_children"] == children == 2
+        assert rep["ns_split"] == 4 * g.n + 8 * children
+        assert rep["node_lists"] == 2 * 20 * (g.n + children) + 16
     finally:
         G.close()
 
