@@ -267,8 +267,12 @@ def serving_bench(args, torch):
     G = [lb.Graph.from_csr(g) for g in cg]
     cand = [np.flatnonzero(g.degrees() > 0).astype(np.int32) for g in cg]
     burst = sv.poisson_schedule(args.serve_queries, float("inf"), [g.n for g in cg], cand, seed=1)
-    outs_a = [torch.empty(cg[r.graph].n, dtype=torch.int32, device="cuda") for r in burst]
-    outs_b = [torch.empty(cg[r.graph].n, dtype=torch.int32, device="cuda") for r in burst]
+
+    def buffers(reqs):
+        # one output per request, sized for that request's graph
+        return [torch.empty(cg[r.graph].n, dtype=torch.int32, device="cuda") for r in reqs]
+
+    outs_a, outs_b = buffers(burst), buffers(burst)
     # one at a time: warm every graph's loop, then the whole burst back to back
     for gi, g in enumerate(G):
         tmp = torch.empty(cg[gi].n, dtype=torch.int32, device="cuda")
@@ -287,12 +291,14 @@ def serving_bench(args, torch):
     exact = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b)) and all(x == 0 for x in st)
     rate = 0.8 * one["qps"]
     pois = sv.poisson_schedule(args.serve_queries, rate, [g.n for g in cg], cand, seed=1)
+    outs_a, outs_b = buffers(pois), buffers(pois)
     one_p = sv.serve_one_at_a_time(G, pois, outs_a)
     srv_p = sv.serve(S, pois, outs_b)
     torch.cuda.synchronize()
     exact_p = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b)) and srv_p["statuses_ok"]
     rate_hi = 0.8 * args.serve_queries / batched_s
     pois_hi = sv.poisson_schedule(args.serve_queries, rate_hi, [g.n for g in cg], cand, seed=2)
+    outs_b = buffers(pois_hi)
     srv_hi = sv.serve(S, pois_hi, outs_b)
     info2 = S.info()
     S.close()

@@ -9,10 +9,13 @@
 #include "lb_device.cuh"
 
 #ifndef LB_WD_MIN_BLOCKS
-#define LB_WD_MIN_BLOCKS 6
+#define LB_WD_MIN_BLOCKS 4
 #endif
 #ifndef LB_WD_WARP_LOOKUP
 #define LB_WD_WARP_LOOKUP 0
+#endif
+#ifndef LB_WD_WALK
+#define LB_WD_WALK 1
 #endif
 
 namespace lbk {
@@ -269,6 +272,103 @@ __device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const No
     }
 }
 
+// Workload decomposition, warp-walk form.  Each warp takes a contiguous
+// slice of tile / 8 edges and walks it 32 edges per step.  One binary search
+// per warp and tile finds the entry of the slice's first edge; after that
+// the warp keeps the current entry in registers and, per step, loads the
+// prefix and first edge of the next 32 entries (coalesced, L1).  An entry
+// starting inside the 32-edge window sets one bit of a mask (entries have
+// at least one edge, so at most 32 start in 32 positions); a lane's entry is
+// the current one plus the number of starts at or before its position, and
+// its prefix / first edge come from the loading lane by shuffle.  That
+// replaces a per-edge search (the bulk of the instructions) by a few
+// warp-wide operations per 32 edges.
+template <bool SSSP, int STEPS>
+__device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt, int64_t E,
+                                        WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
+                                        uint32_t *status, uint32_t level, uint32_t stamp) {
+    const int64_t T = p.tile;
+    const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
+    const int64_t ntiles = (E + T - 1) / T;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t e0 = t * T;
+        const int64_t e1 = min(e0 + T, E);
+        int64_t i0 = __ldg(in.tstart + t);
+        int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldg(in.tstart + t + 1) + 1, in_cnt) : in_cnt;
+        if (i0 < 0 || i0 >= ihi) {
+            if (lane == 0) atomicOr(&ctl->error, kErrBounds);
+            i0 = 0;
+            ihi = in_cnt;
+        }
+        const int64_t w0 = e0 + (int64_t)warp * W;
+        const int64_t w1 = min(w0 + W, e1);
+        if (w0 >= w1) continue;  // warp-uniform
+        int64_t kcur = list_search(in.scan, i0, ihi, w0);
+        int64_t scur = __ldg(in.scan + kcur);
+        int64_t bcur = __ldg(in.beg + kcur);
+        int32_t ucur = SSSP ? __ldg(in.v + kcur) : 0;
+        for (int64_t ew = w0; ew < w1; ew += 32 * STEPS) {
+            int32_t vv[STEPS];
+            uint32_t ww[STEPS], dd[STEPS];
+            bool ok[STEPS];
+#pragma unroll
+            for (int st = 0; st < STEPS; ++st) {
+                const int64_t es = ew + 32 * st;  // first edge of this step (uniform)
+                const int64_t e = es + lane;
+                ok[st] = false;
+                vv[st] = 0;
+                ww[st] = 0;
+                dd[st] = 0;
+                if (es >= w1) continue;  // warp-uniform
+                const int64_t j = kcur + 1 + lane;
+                int64_t sj = INT64_MAX, bj = 0;
+                int32_t uj = 0;
+                if (j < ihi) {
+                    sj = __ldg(in.scan + j);
+                    bj = __ldg(in.beg + j);
+                    if (SSSP) uj = __ldg(in.v + j);
+                }
+                const int64_t pos = sj - es;  // >= 1: entry j starts after es
+                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
+                const int c = __popc(starts & upto);
+                const int src_lane = c > 0 ? c - 1 : 0;
+                const int64_t s_sh = __shfl_sync(kFull, sj, src_lane);
+                const int64_t b_sh = __shfl_sync(kFull, bj, src_lane);
+                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
+                const int64_t s_l = c > 0 ? s_sh : scur;
+                const int64_t b_l = c > 0 ? b_sh : bcur;
+                // advance to the entry holding the next step's first edge
+                const int adv = __popc(__ballot_sync(kFull, sj <= es + 32));
+                if (adv > 0) {
+                    scur = __shfl_sync(kFull, sj, adv - 1);
+                    bcur = __shfl_sync(kFull, bj, adv - 1);
+                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
+                    kcur += adv;
+                }
+                if (e < w1) {
+                    const int64_t eidx = b_l + (e - s_l);
+                    if ((uint64_t)eidx >= (uint64_t)p.g.m) {
+                        atomicOr(&ctl->error, kErrBounds);
+                    } else {
+                        ok[st] = true;
+                        vv[st] = __ldg(p.g.col + eidx);
+                        if (SSSP) {
+                            ww[st] = __ldg(p.g.w + eidx);
+                            const int32_t u = c > 0 ? u_sh : ucur;
+                            dd[st] = sssp_source_dist(status, p.epoch, u, stamp);
+                        }
+                    }
+                }
+            }
+            relax_items<SSSP, STEPS, kOutNode, true>(ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status, level, stamp,
+                                                     &ctl->error, wb, ws, cnt, o);
+        }
+    }
+}
+
 template <bool SSSP, int ITEMS>
 __global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams p) {
     __shared__ WarpBuf s_wb[kWarps];
@@ -293,7 +393,11 @@ __global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams
     o.pushes = &ctl->pushes;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
+#if LB_WD_WALK
+    wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
+#else
     wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
+#endif
     wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }

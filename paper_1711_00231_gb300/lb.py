@@ -156,6 +156,19 @@ def _ptr(x) -> Optional[int]:
     raise TypeError(f"unsupported buffer type {type(x)}")
 
 
+def _need(buf, count: int, what: str = "output") -> None:
+    """Device buffers cannot be checked by the C ABI: refuse one that is
+    smaller than the graph before the kernels write past its end."""
+    if buf is None:
+        return
+    have = buf.numel() if hasattr(buf, "numel") else np.asarray(buf).size
+    if have < count:
+        raise ValueError(f"{what} buffer holds {have} elements, the graph needs {count}")
+    esz = buf.element_size() if hasattr(buf, "element_size") else np.asarray(buf).itemsize
+    if esz != 4:
+        raise ValueError(f"{what} buffer must have 4-byte elements")
+
+
 def _stream_handle(stream) -> Optional[int]:
     if stream is None:
         return None
@@ -303,6 +316,8 @@ def lb_bfs_wd_noalloc(offsets_dev, cols_dev, n: int, m: int, src: int, levels_de
     callers whose GPU memory belongs to another allocator or that must not
     call cudaMalloc while serving.  Scratch comes from a fixed array inside
     the library; n <= 131072, m <= 16777216."""
+    if n <= (1 << 17) and m <= (1 << 24):
+        _need(levels_dev, n, "levels")
     _check(_load().lb_bfs_wd_noalloc(_ptr(offsets_dev), _ptr(cols_dev), n, m, src, _ptr(levels_dev),
                                      _stream_handle(stream)))
 
@@ -433,9 +448,13 @@ class Graph:
         return out, rc
 
     def bfs_dev(self, src, strategy, out_dev, parents_dev=None, stream=None):
+        _need(out_dev, self.n)
+        _need(parents_dev, self.n, "parents")
         lb_bfs_dev(self.h, src, strategy, out_dev, parents_dev, stream)
 
     def sssp_dev(self, src, strategy, out_dev, parents_dev=None, stream=None):
+        _need(out_dev, self.n)
+        _need(parents_dev, self.n, "parents")
         lb_sssp_dev(self.h, src, strategy, out_dev, parents_dev, stream)
 
     def stats(self) -> dict:

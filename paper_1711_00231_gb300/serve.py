@@ -38,6 +38,8 @@ class Server:
         self.h = lb.lb_server_create([g.h for g in self.graphs], slots, ctas_per_sm, tile, idle_us, mem_fraction)
 
     def submit(self, graph: int, src: int, kind: str, out_dev) -> int:
+        if 0 <= graph < len(self.graphs):
+            lb._need(out_dev, self.graphs[graph].n)
         return lb.lb_server_submit(self.h, graph, src, KIND[kind], out_dev)
 
     def poll(self):
