@@ -340,6 +340,7 @@ __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const Nod
                 const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
                 const int64_t s_l = c > 0 ? s_sh : scur;
                 const int64_t b_l = c > 0 ? b_sh : bcur;
+                const int32_t u_l = c > 0 ? u_sh : ucur;  // taken before the walk advances
                 // advance to the entry holding the next step's first edge
                 const int adv = __popc(__ballot_sync(kFull, sj <= es + 32));
                 if (adv > 0) {
@@ -357,8 +358,7 @@ __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const Nod
                         vv[st] = __ldg(p.g.col + eidx);
                         if (SSSP) {
                             ww[st] = __ldg(p.g.w + eidx);
-                            const int32_t u = c > 0 ? u_sh : ucur;
-                            dd[st] = sssp_source_dist(status, p.epoch, u, stamp);
+                            dd[st] = sssp_source_dist(status, p.epoch, u_l, stamp);
                         }
                     }
                 }
