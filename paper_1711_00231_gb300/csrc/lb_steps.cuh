@@ -554,7 +554,11 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     WarpScratch &ws = s_ws[warp];
     uint32_t cnt = 0, scnt = 0;
     if (kind == 2u) {
+#if LB_WD_WALK
+        wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
+#else
         wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
+#endif
     } else {
         const int64_t mdt = p.mdt;
         const int64_t stride = (int64_t)gridDim.x * kBlock;

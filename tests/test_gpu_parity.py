@@ -145,6 +145,19 @@ def test_rmat20_bfs_sssp_all_strategies():
     run_all(g, [gg.max_degree_vertex(g)])
 
 
+def test_erdos_renyi_er20_shape():
+    # ER20 of Table II: 1.05M nodes, 4.19M edges (random degrees, low diameter, no small-world skew)
+    g = gg.erdos_renyi(1 << 20, 4194304, seed=1)
+    srcs = gg.pick_sources(g, 2, seed=1).tolist()
+    run_all(g, srcs, strategies=["BS", "EP", "WD", "NS", "HP", "NS_PHYS"])
+    mdt, maxdeg, b, _ = oracle.mdt(g.offsets, 10)
+    G = lb.Graph.from_csr(g)
+    try:
+        assert G.mdt(10) == (mdt, maxdeg, b)
+    finally:
+        G.close()
+
+
 def test_grid4096_sssp_from_corner():
     # 4096 x 4096 grid, weights U[1,1000], source at the corner
     g = gg.grid(4096, 4096, seed=1)

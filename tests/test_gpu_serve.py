@@ -131,10 +131,13 @@ def test_overflow_and_invalid_requests(mix):
         assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.dijkstra(g, 0)[0])
         with pytest.raises(lb.LbError):
             S.submit(0, 9, "bfs", out)            # source out of range
+        out1 = torch.empty(graphs[4].n, dtype=torch.int32, device="cuda")
         with pytest.raises(lb.LbError):
-            S.submit(1, 0, "sssp", out)           # unweighted graph
+            S.submit(1, 0, "sssp", out1)          # unweighted graph
         with pytest.raises(lb.LbError):
             S.submit(5, 0, "bfs", out)            # no such graph
+        with pytest.raises(ValueError):
+            S.submit(1, 0, "bfs", out)            # output smaller than the graph
     finally:
         S.close()
         G.close()
