@@ -87,8 +87,10 @@ typedef struct lb_options {
                               conditional WHILE node); 1: host loop with a
                               worklist-size readback per iteration, as in the
                               paper's drivers (0) */
-    int32_t wd_tile;       /* worklist edges per WD tile: 256..8192, a
-                              multiple of 256 (2048) */
+    int32_t wd_tile;       /* largest WD tile in worklist edges: 256..8192,
+                              a multiple of 256 (2048); each iteration uses
+                              the smallest multiple of 256 up to this that
+                              gives every CTA about two tiles */
     int32_t ctas_per_sm;   /* CTAs per SM the fixed relax grid is sized for;
                               0 = the occupancy limit */
     int32_t reserved[10];
@@ -104,7 +106,8 @@ typedef struct lb_mem_stats {
     int64_t visited;       /* BFS visited bitmap + SSSP per-iteration stamps */
     int64_t node_lists;    /* node worklists (two buffers: id, first edge,
                               edge prefix) */
-    int64_t tile_starts;   /* WD/HP: first worklist entry of every tile */
+    int64_t tile_starts;   /* WD/HP: worklist entry holding every 256th
+                              worklist edge (tile starts) */
     int64_t coo_src;       /* EP: COO source array (COO dst/wt are the CSR
                               cols/weights arrays, not duplicated) */
     int64_t edge_lists;    /* EP: edge worklists (two buffers of m ids) */
@@ -309,7 +312,7 @@ lb_status lb_server_stop(lb_server *s);
  * receives hop counts, -1 unreachable) are caller-owned device pointers on
  * the current device; no lb_graph is used and the CSR is not validated.
  * All other memory comes from one fixed array of device memory inside the
- * library (about 5.4 MiB; every GPU that loads the library holds it until
+ * library (about 5.9 MiB; every GPU that loads the library holds it until
  * the process exits), so the call allocates nothing.  Limits: n <= 131072
  * and m <= 16777216; larger sizes return LB_ERR_ARG.  The first call on a
  * device looks the array up (cudaGetSymbolAddress) and should come before

@@ -81,7 +81,8 @@ constexpr int kStrategies = 7;
 
 bool is_ep(int s) { return s == LB_EP || s == LB_EP_NOCHUNK; }
 
-int64_t round_tiles(int64_t m, int64_t tile) { return m / tile + 2; }
+// tile-start entries a list needs: one per kTileGrain worklist edges
+int64_t round_tiles(int64_t m) { return m / kTileGrain + 2; }
 
 }  // namespace
 
@@ -326,7 +327,7 @@ lb_status ensure_workspace(lb_graph *g, int s) {
     }
     const int64_t cap = node_list_cap(g, s);
     const bool tiles = (s == LB_WD || s == LB_HP);
-    const int64_t tcap = round_tiles(g->m, g->opt.wd_tile);
+    const int64_t tcap = round_tiles(g->m);
     if (g->list_cap < cap || (tiles && (!g->have_tiles || g->tile_cap != tcap))) {
         quiesce(g);
         drop_execs(g);
@@ -774,7 +775,7 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
     out->base_total = out->csr_offsets + out->csr_cols + out->csr_weights;
     out->status = 4 * n;
     out->visited = 4 * ((n + 31) / 32) + 4 * n;
-    const int64_t tcap = round_tiles(m, g->opt.wd_tile);
+    const int64_t tcap = round_tiles(m);
     if (s == LB_NS || s == LB_NS_PHYS || s == LB_HP) {
         LB_TRY(ensure_mdt(g));
         out->mdt = g->mdt;

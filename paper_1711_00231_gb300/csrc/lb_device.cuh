@@ -50,7 +50,7 @@ struct FlushOut {
     const int32_t *child_first;  // kOutPhys: first child id of each split node
     int64_t cap;       // entries the output can hold
     int64_t tile_cap;  // tstart entries
-    int32_t tile;
+    int32_t tile;      // edges between recorded tile starts (kTileGrain in the hot path)
     int32_t mdt;
 };
 
@@ -361,6 +361,17 @@ __device__ __forceinline__ void finish_plain_step(const StepParams &p, Ctl *ctl,
     ctl->blocks_done = 0;
     set_loop(p, ctl, cnt > 0);
     __threadfence();
+}
+
+// Tile size of an iteration over E list edges on `grid` CTAs: the smallest
+// multiple of kTileGrain (at most max_tile) that still gives every CTA about
+// two tiles, so small lists spread over the grid and large ones keep long
+// tiles.
+__device__ __forceinline__ int64_t iteration_tile(int64_t E, int64_t grid, int64_t max_tile) {
+    const int64_t qmax = max_tile / kTileGrain > 0 ? max_tile / kTileGrain : 1;
+    int64_t q = (E + kTileGrain * 2 * grid - 1) / (kTileGrain * 2 * grid);
+    q = q < 1 ? 1 : (q > qmax ? qmax : q);
+    return q * kTileGrain;
 }
 
 // Largest k in [lo, hi) with scan[k] <= e (read-only list, L1-cached).

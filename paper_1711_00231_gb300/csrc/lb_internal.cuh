@@ -24,6 +24,10 @@ constexpr uint32_t kSat = 0xFFFFFFFEu;  // saturated distance (>= 2^32 - 2)
 constexpr int kBlock = 256;             // threads per CTA of every step kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kTraceMax = 4096;
+// Tile starts are recorded every kTileGrain worklist edges; an iteration
+// then cuts its list into tiles of q * kTileGrain edges, q chosen from the
+// list's size so that small lists still spread over many CTAs.
+constexpr int64_t kTileGrain = 256;
 
 // error bits in Ctl::error
 enum : uint32_t {
@@ -114,9 +118,9 @@ struct StepParams {
     uint32_t *child_dist;        // NS_PHYS: mirrored distance of child n + i
     int64_t n_children;          // NS_PHYS: children created at p.mdt
     int64_t list_cap;
-    int64_t tile_cap;
+    int64_t tile_cap;   // tile-start entries per list (one per kTileGrain edges)
     int64_t elist_cap;
-    int32_t tile;
+    int32_t tile;       // largest tile (edges) an iteration may use
     int32_t mdt;
     int32_t hp_threshold;  // <= 0: never switch to WD
     int32_t strategy;

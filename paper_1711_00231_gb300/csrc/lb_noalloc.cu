@@ -10,7 +10,7 @@
 // state) in one fixed-size array of device memory declared in this file.
 // Each GPU that loads the library holds that array until the process exits.
 //
-// Limits: n <= 131072 vertices and m <= 16777216 edges (about 5.4 MiB of
+// Limits: n <= 131072 vertices and m <= 16777216 edges (about 5.9 MiB of
 // scratch).  Every call on a device shares the array and finds the previous
 // call's contents in it; the kernels reset what must start at zero (loop
 // counters, the visited bitmap and the output levels).  Calls whose work
@@ -29,7 +29,7 @@ namespace {
 constexpr int64_t kNaMaxN = (int64_t)1 << 17;
 constexpr int64_t kNaMaxM = (int64_t)1 << 24;
 constexpr int32_t kNaTile = 2048;
-constexpr int64_t kNaTiles = kNaMaxM / kNaTile + 2;
+constexpr int64_t kNaTiles = kNaMaxM / kTileGrain + 2;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -109,7 +109,7 @@ extern "C" lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t
         p.lists[b].tstart = (int32_t *)(L + kListV + kListBeg + kListScan);
     }
     p.list_cap = n;
-    p.tile_cap = m / kNaTile + 2;
+    p.tile_cap = m / kTileGrain + 2;
     p.tile = kNaTile;
     p.mdt = 1;
     p.hp_threshold = 0;

@@ -74,6 +74,7 @@ struct HostShared {
 struct Slot {
     unsigned long long claim;  // generation << 32 | next tile
     uint32_t job_gen;          // generation the job fields below belong to
+    uint32_t job_q;            // RELAX: tile = job_q * kTileGrain edges
     uint32_t job_kind;
     uint32_t job_tiles;
     uint32_t job_done;
@@ -204,10 +205,11 @@ __device__ __forceinline__ SlotState slot_state(const Slot *S) {
 
 // Opens the slot's next job (single thread).  Parameters are written before
 // the claim word moves to the new generation.
-__device__ void open_job(Slot *S, uint32_t kind, uint32_t tiles) {
+__device__ void open_job(Slot *S, uint32_t kind, uint32_t tiles, uint32_t q = 1) {
     const unsigned long long w = atomicAdd(&S->claim, 0ull);
     const uint32_t gen = (uint32_t)(w >> 32) + 1u;
     S->job_gen = gen;
+    S->job_q = q;
     S->job_kind = kind;
     S->job_tiles = tiles;
     S->job_done = 0;
@@ -266,11 +268,12 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
         L.beg[0] = beg;
         L.scan[0] = 0;
         L.scan[1] = deg;
-        const int64_t tiles = (deg + T - 1) / T;
-        for (int64_t k = 0; k < tiles && k < P.tile_cap; ++k) L.tstart[k] = 0;
+        const int64_t grains = (deg + kTileGrain - 1) / kTileGrain;
+        for (int64_t k = 0; k < grains && k < P.tile_cap; ++k) L.tstart[k] = 0;
         S->in_cnt = 1;
         S->in_edges = (uint64_t)deg;
-        open_job(S, kJobRelax, (uint32_t)tiles);
+        const int64_t Tj = iteration_tile(deg, gridDim.x, T);
+        open_job(S, kJobRelax, (uint32_t)((deg + Tj - 1) / Tj), (uint32_t)(Tj / kTileGrain));
         return;
     }
     if (kind == kJobRelax) {
@@ -288,7 +291,8 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
             S->in_cnt = (uint32_t)cnt;
             S->in_edges = (uint64_t)edges;
             S->out_pack = 0ull;
-            open_job(S, kJobRelax, (uint32_t)((edges + T - 1) / T));
+            const int64_t Tj = iteration_tile(edges, gridDim.x, T);
+            open_job(S, kJobRelax, (uint32_t)((edges + Tj - 1) / Tj), (uint32_t)(Tj / kTileGrain));
             return;
         }
         if (cnt > 0 && !(err & (kErrCapacity | kErrBounds))) atomicOr(&S->error, kErrIterCap);
@@ -350,16 +354,17 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, WarpBuf &wb, War
     o.pack = &S->out_pack;
     o.cap = P.slot_cap;
     o.tile_cap = P.tile_cap;
-    o.tile = P.tile;
+    o.tile = (int32_t)kTileGrain;
     o.mdt = 1;
     o.err = &S->error;
     o.pushes = &S->pushes;
-    const int64_t T = P.tile;
+    const int64_t q = ((const volatile Slot *)S)->job_q;
+    const int64_t T = q * kTileGrain;
     const int64_t ntiles = (E + T - 1) / T;
     const int64_t e0 = t * T;
     const int64_t e1 = min(e0 + T, E);
-    int64_t i0 = __ldcg(in.tstart + t);
-    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldcg(in.tstart + t + 1) + 1, in_cnt) : in_cnt;
+    int64_t i0 = __ldcg(in.tstart + t * q);
+    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldcg(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
     if (i0 < 0 || i0 >= ihi) {
         if (threadIdx.x == 0) atomicOr(&S->error, kErrBounds);
         return;
@@ -730,7 +735,7 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
         if (m > s->slot_m) s->slot_m = m;
     }
     s->slot_cap = s->slot_n;
-    s->tile_cap = s->slot_m / o.tile + 2;
+    s->tile_cap = s->slot_m / kTileGrain + 2;
     // per slot: bitmap + stamps + two worklists (v, beg, scan, tile starts)
     const int64_t per_list = 4 * s->slot_cap + 8 * s->slot_cap + 8 * (s->slot_cap + 1) + 4 * s->tile_cap;
     s->slot_bytes = 4 * ((s->slot_n + 31) / 32) + 4 * s->slot_n + 2 * per_list + 4096;

@@ -9,14 +9,9 @@
 #include "lb_device.cuh"
 
 #ifndef LB_WD_MIN_BLOCKS
-#define LB_WD_MIN_BLOCKS 4
+#define LB_WD_MIN_BLOCKS 6
 #endif
-#ifndef LB_WD_WARP_LOOKUP
-#define LB_WD_WARP_LOOKUP 0
-#endif
-#ifndef LB_WD_WALK
-#define LB_WD_WALK 1
-#endif
+
 
 namespace lbk {
 
@@ -43,7 +38,7 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
     o.pack = &ctl->out_pack;
     o.cap = p.list_cap;
     o.tile_cap = p.tile_cap;
-    o.tile = p.tile;
+    o.tile = (int32_t)kTileGrain;
     o.mdt = p.mdt;
     o.err = &ctl->error;
     o.pushes = &ctl->pushes;
@@ -118,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
     o.pack = &ctl->out_pack;
     o.cap = p.list_cap;
     o.tile_cap = p.tile_cap;
-    o.tile = p.tile;
+    o.tile = (int32_t)kTileGrain;
     o.mdt = p.mdt;
     o.err = &ctl->error;
     o.pushes = &ctl->pushes;
@@ -194,86 +189,13 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Workload decomposition over CTA tiles.  The input list's edges (in list
-// order) are cut into tiles of p.tile edges; tile t starts in entry
-// tstart[t] (written by the push that created the list).  Inside a tile,
-// consecutive lanes take consecutive edges, so a node's adjacency is read
-// coalesced.  A warp finds the entries of its 32 edges together: one
-// warp-uniform binary search over the tile's slice of the edge prefix gives
-// the entry of the first edge; every later entry that starts inside the
-// 32-edge window sets one bit of a mask (each entry has at least one edge,
-// so the window holds at most 32 starts), and a lane's entry is the first
-// one plus the number of starts at or before its position.
-// ---------------------------------------------------------------------------
-template <bool SSSP, int ITEMS>
-__device__ __forceinline__ void wd_tiles(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt,
-                                         int64_t E, WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
-                                         uint32_t *status, uint32_t level, uint32_t stamp) {
-    const int64_t T = p.tile;
-    const int64_t ntiles = (E + T - 1) / T;
-    const uint32_t lane = lane_id();
-    const int64_t wbase = (int64_t)(threadIdx.x & ~31u);
-    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
-    (void)upto;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t e0 = t * T;
-        const int64_t e1 = min(e0 + T, E);
-        int64_t i0 = __ldg(in.tstart + t);
-        int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldg(in.tstart + t + 1) + 1, in_cnt) : in_cnt;
-        if (i0 < 0 || i0 >= ihi) {  // inconsistent tile start: flag, fall back to the whole list
-            if (threadIdx.x == 0) atomicOr(&ctl->error, kErrBounds);
-            i0 = 0;
-            ihi = in_cnt;
-        }
-        for (int64_t r0 = e0; r0 < e1; r0 += (int64_t)kBlock * ITEMS) {
-            int32_t vv[ITEMS];
-            uint32_t ww[ITEMS], dd[ITEMS];
-            bool ok[ITEMS];
-#pragma unroll
-            for (int it = 0; it < ITEMS; ++it) {
-                const int64_t ew = r0 + (int64_t)it * kBlock + wbase;  // the warp's first edge
-                const int64_t e = ew + lane;
-                ok[it] = false;
-                vv[it] = 0;
-                ww[it] = 0;
-                dd[it] = 0;
-                if (ew < e1) {  // warp-uniform
-#if LB_WD_WARP_LOOKUP
-                    const int64_t kf = list_search(in.scan, i0, ihi, ew);
-                    const int64_t j = kf + 1 + lane;
-                    uint32_t bit = 0;
-                    if (j < ihi) {
-                        const int64_t pos = __ldg(in.scan + j) - ew;
-                        if (pos < 32) bit = 1u << pos;
-                    }
-                    const uint32_t starts = __reduce_or_sync(kFull, bit);
-                    const int64_t k = kf + __popc(starts & upto);
-#else
-                    const int64_t k = e < e1 ? list_search(in.scan, i0, ihi, e) : i0;
-#endif
-                    if (e < e1) {
-                        const int64_t eidx = __ldg(in.beg + k) + (e - __ldg(in.scan + k));
-                        if ((uint64_t)eidx >= (uint64_t)p.g.m) {
-                            atomicOr(&ctl->error, kErrBounds);
-                        } else {
-                            ok[it] = true;
-                            vv[it] = __ldg(p.g.col + eidx);
-                            if (SSSP) {
-                                ww[it] = __ldg(p.g.w + eidx);
-                                dd[it] = sssp_source_dist(status, p.epoch, __ldg(in.v + k), stamp);
-                            }
-                        }
-                    }
-                }
-            }
-            relax_items<SSSP, ITEMS, kOutNode, true>(ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status, level, stamp,
-                                                     &ctl->error, wb, ws, cnt, o);
-        }
-    }
-}
-
-// Workload decomposition, warp-walk form.  Each warp takes a contiguous
-// slice of tile / 8 edges and walks it 32 edges per step.  One binary search
+// Workload decomposition (Sec. III-A) over CTA tiles.  The input list's
+// edges (in list order) are cut into tiles of T edges; the push that built
+// the list recorded the entry holding every kTileGrain-th list edge, so tile
+// t starts in entry tstart[t * T / kTileGrain] (the paper's NodeOffset /
+// EdgeOffset, found without a scan or an offset kernel).  Each warp takes a
+// contiguous slice of T / 8 edges and walks it 32 edges per step, so
+// consecutive lanes read consecutive edges of a node (coalesced).  One binary search
 // per warp and tile finds the entry of the slice's first edge; after that
 // the warp keeps the current entry in registers and, per step, loads the
 // prefix and first edge of the next 32 entries (coalesced, L1).  An entry
@@ -287,7 +209,8 @@ template <bool SSSP, int STEPS>
 __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt, int64_t E,
                                         WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
                                         uint32_t *status, uint32_t level, uint32_t stamp) {
-    const int64_t T = p.tile;
+    const int64_t T = iteration_tile(E, gridDim.x, p.tile);
+    const int64_t q = T / kTileGrain;
     const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
     const int64_t ntiles = (E + T - 1) / T;
     const uint32_t lane = lane_id();
@@ -296,8 +219,8 @@ __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const Nod
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t e0 = t * T;
         const int64_t e1 = min(e0 + T, E);
-        int64_t i0 = __ldg(in.tstart + t);
-        int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldg(in.tstart + t + 1) + 1, in_cnt) : in_cnt;
+        int64_t i0 = __ldg(in.tstart + t * q);
+        int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldg(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
         if (i0 < 0 || i0 >= ihi) {
             if (lane == 0) atomicOr(&ctl->error, kErrBounds);
             i0 = 0;
@@ -387,17 +310,13 @@ __global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams
     o.pack = &ctl->out_pack;
     o.cap = p.list_cap;
     o.tile_cap = p.tile_cap;
-    o.tile = p.tile;
+    o.tile = (int32_t)kTileGrain;
     o.mdt = p.mdt;
     o.err = &ctl->error;
     o.pushes = &ctl->pushes;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
-#if LB_WD_WALK
     wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
-#else
-    wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
-#endif
     wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }
@@ -425,7 +344,7 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
     o.pack = &ctl->out_pack;
     o.cap = p.elist_cap;
     o.tile_cap = 0;
-    o.tile = p.tile;
+    o.tile = (int32_t)kTileGrain;
     o.mdt = p.mdt;
     o.err = &ctl->error;
     o.pushes = &ctl->pushes;
@@ -541,7 +460,7 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     osup.pack = &ctl->out_pack;
     osup.cap = p.list_cap;
     osup.tile_cap = p.tile_cap;
-    osup.tile = p.tile;
+    osup.tile = (int32_t)kTileGrain;
     osup.mdt = p.mdt;
     osup.err = &ctl->error;
     osup.pushes = &ctl->pushes;
@@ -554,11 +473,7 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     WarpScratch &ws = s_ws[warp];
     uint32_t cnt = 0, scnt = 0;
     if (kind == 2u) {
-#if LB_WD_WALK
         wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
-#else
-        wd_tiles<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
-#endif
     } else {
         const int64_t mdt = p.mdt;
         const int64_t stride = (int64_t)gridDim.x * kBlock;

@@ -136,7 +136,7 @@ __global__ void k_init(StepParams p) {
         L.scan[deg > 0 ? 1 : 0] = deg;
     }
     if (L.tstart != nullptr) {
-        const int64_t tiles = (deg + p.tile - 1) / p.tile;
+        const int64_t tiles = (deg + kTileGrain - 1) / kTileGrain;
         for (int64_t k = tid; k < tiles && k < p.tile_cap; k += stride) L.tstart[k] = 0;
     }
 }
