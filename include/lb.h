@@ -312,7 +312,7 @@ lb_status lb_server_stop(lb_server *s);
  * receives hop counts, -1 unreachable) are caller-owned device pointers on
  * the current device; no lb_graph is used and the CSR is not validated.
  * All other memory comes from one fixed array of device memory inside the
- * library (about 5.9 MiB; every GPU that loads the library holds it until
+ * library (about 3.6 MiB; every GPU that loads the library holds it until
  * the process exits), so the call allocates nothing.  Limits: n <= 131072
  * and m <= 16777216; larger sizes return LB_ERR_ARG.  The first call on a
  * device looks the array up (cudaGetSymbolAddress) and should come before

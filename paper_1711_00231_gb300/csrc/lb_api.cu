@@ -787,9 +787,9 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
         out->edge_lists = 2 * 4 * (m > 0 ? m : 1);
     } else {
         const int64_t cap = node_list_cap(g, s);
-        out->node_lists = 2 * (4 * cap + 8 * cap + 8 * (cap + 1));
+        out->node_lists = 2 * (4 * cap + 4 * cap + 4 * (cap + 1));
         if (s == LB_WD || s == LB_HP) out->tile_starts = 2 * 4 * tcap;
-        if (s == LB_HP) out->sub_lists = 2 * (4 * n + 8 * n + 8 * (n + 1) + 4 * tcap);
+        if (s == LB_HP) out->sub_lists = 2 * (4 * n + 4 * n + 4 * (n + 1) + 4 * tcap);
     }
     out->control = (int64_t)sizeof(Ctl);
     out->extra_total = out->status + out->visited + out->node_lists + out->tile_starts + out->coo_src +
@@ -918,7 +918,7 @@ lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_
     LB_CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     void *bufs[7] = {nullptr};
     const size_t sizes[7] = {sizeof(int64_t) * (size_t)(F > 0 ? F : 1), sizeof(int32_t) * (size_t)(F > 0 ? F : 1),
-                             sizeof(int64_t) * (size_t)(F > 0 ? F : 1), sizeof(int64_t) * (size_t)(F + 1),
+                             sizeof(int32_t) * (size_t)(F > 0 ? F : 1), sizeof(int32_t) * (size_t)(F + 1),
                              sizeof(int32_t) * (size_t)(T + 1), sizeof(Ctl), sizeof(int64_t)};
     lb_status status = LB_OK;
     cudaError_t e = cudaSuccess;
@@ -927,11 +927,11 @@ lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_
     if (e == cudaSuccess && F > 0) e = cudaMemcpyAsync(bufs[0], deg, sizes[0], cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bufs[5], 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bufs[4], 0, sizes[4], st);
-    NodeList L{(int32_t *)bufs[1], (int64_t *)bufs[2], (int64_t *)bufs[3], (int32_t *)bufs[4]};
+    NodeList L{(int32_t *)bufs[1], (int32_t *)bufs[2], (int32_t *)bufs[3], (int32_t *)bufs[4]};
     if (e == cudaSuccess) e = launch_wd_offsets((const int64_t *)bufs[0], F, T, L, (Ctl *)bufs[5], (int64_t *)bufs[6], st);
     int64_t h_ept = 0;
     int32_t *h_ts = new (std::nothrow) int32_t[(size_t)T + 1];
-    int64_t *h_scan = new (std::nothrow) int64_t[(size_t)F + 1];
+    int32_t *h_scan = new (std::nothrow) int32_t[(size_t)F + 1];
     if (!h_ts || !h_scan) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_ept, bufs[6], sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_ts, bufs[4], sizes[4], cudaMemcpyDeviceToHost, st);

@@ -31,7 +31,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2, kOutEdgesPerEdge = 3, kOutPhys = 4 };
 
 struct WarpBuf {
-    int64_t beg[kWB];
+    int32_t beg[kWB];
     int32_t v[kWB];
     uint32_t deg[kWB];
 };
@@ -73,11 +73,12 @@ __device__ __forceinline__ uint32_t out_units(uint32_t deg, int32_t mdt) {
 // Warp-uniform: every lane of the warp calls it with the same cnt.
 // Requires cnt + 32 <= kWB on entry.
 __device__ __forceinline__ void wpush(WarpBuf &b, uint32_t &cnt, bool want, int32_t v, int64_t beg, uint32_t deg) {
+    // beg < m < 2^31: stored in 32 bits
     const unsigned m = __ballot_sync(kFull, want);
     if (want) {
         const uint32_t s = cnt + __popc(m & lanemask_lt());
         b.v[s] = v;
-        b.beg[s] = beg;
+        b.beg[s] = (int32_t)beg;
         b.deg[s] = deg;
     }
     cnt += __popc(m);
@@ -133,7 +134,7 @@ __device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const F
             const int64_t S = ebase + s.pe[i];
             o.list.v[pos] = b.v[i];
             o.list.beg[pos] = b.beg[i];
-            o.list.scan[pos] = S;
+            o.list.scan[pos] = (int32_t)S;
             if (TILED) {
                 const int64_t E = S + b.deg[i];
                 for (int64_t k = (S + o.tile - 1) / o.tile; k * o.tile < E; ++k)
@@ -148,8 +149,8 @@ __device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const F
                 const int64_t pos = ubase + j;
                 // a physically split node's runs after the first belong to its children
                 o.list.v[pos] = (KIND == kOutPhys && k > 0) ? __ldg(o.child_first + b.v[i]) + (int32_t)(k - 1) : b.v[i];
-                o.list.beg[pos] = b.beg[i] + k * o.mdt;
-                o.list.scan[pos] = ebase + s.pe[i] + k * o.mdt;
+                o.list.beg[pos] = (int32_t)(b.beg[i] + k * o.mdt);
+                o.list.scan[pos] = (int32_t)(ebase + s.pe[i] + k * o.mdt);
             } else {
                 o.elist[ubase + j] = (int32_t)(b.beg[i] + k);
             }
@@ -201,7 +202,14 @@ __device__ __forceinline__ uint32_t sssp_source_dist(const uint32_t *__restrict_
 // every atomic, then every offset load of a won vertex, then the pushes --
 // so the latencies of the items overlap instead of queueing behind one
 // another (a warp-synchronous push between items would serialise them).
-template <bool SSSP, int ITEMS, int KIND, bool TILED>
+// Loads of data other CTAs write: plain (L1) inside a single-iteration
+// launch, L2-coherent (ld.global.cg) inside the persistent serving kernel.
+template <bool COH>
+__device__ __forceinline__ uint32_t ld_mut(const uint32_t *p) {
+    return COH ? __ldcg(p) : *p;
+}
+
+template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false>
 __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32_t (&vv)[ITEMS],
                                             const uint32_t (&ww)[ITEMS], const uint32_t (&dd)[ITEMS],
                                             const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
@@ -219,9 +227,9 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
             if (dd[it] == kInf) continue;
             const uint64_t a64 = (uint64_t)dd[it] + (uint64_t)ww[it];
             val[it] = a64 >= kSat ? kSat : (uint32_t)a64;
-            cand[it] = val[it] < status[vv[it]];
+            cand[it] = val[it] < ld_mut<COH>(status + vv[it]);
         } else {
-            cand[it] = !(bitmap[(uint32_t)vv[it] >> 5] & (1u << ((uint32_t)vv[it] & 31u)));
+            cand[it] = !(ld_mut<COH>(bitmap + ((uint32_t)vv[it] >> 5)) & (1u << ((uint32_t)vv[it] & 31u)));
         }
     }
     uint32_t prev[ITEMS];
@@ -247,7 +255,7 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
         // queue only the first improvement of v in this iteration
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it)
-            if (won[it] && epoch[vv[it]] == stamp) won[it] = false;
+            if (won[it] && ld_mut<COH>(epoch + vv[it]) == stamp) won[it] = false;
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it)
             if (won[it]) prev[it] = atomicExch(&epoch[vv[it]], stamp);
@@ -351,7 +359,7 @@ __device__ __forceinline__ void finish_plain_step(const StepParams &p, Ctl *ctl,
     trace_append(ctl, kModeRelax, ctl->in_cnt, step_edges);
     ctl->relaxed += (unsigned long long)step_edges;
     const uint32_t out = ctl->par ^ 1u;
-    if (node_list) p.lists[out].scan[cnt] = edges;
+    if (node_list) p.lists[out].scan[cnt] = (int32_t)edges;
     ctl->par = out;
     ctl->in_cnt = (uint32_t)cnt;
     ctl->in_edges = (uint64_t)edges;
@@ -375,7 +383,7 @@ __device__ __forceinline__ int64_t iteration_tile(int64_t E, int64_t grid, int64
 }
 
 // Largest k in [lo, hi) with scan[k] <= e (read-only list, L1-cached).
-__device__ __forceinline__ int64_t list_search(const int64_t *__restrict__ scan, int64_t lo, int64_t hi, int64_t e) {
+__device__ __forceinline__ int64_t list_search(const int32_t *__restrict__ scan, int64_t lo, int64_t hi, int64_t e) {
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
         if (__ldg(scan + mid) <= e) lo = mid; else hi = mid;

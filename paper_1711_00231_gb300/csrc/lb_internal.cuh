@@ -4,7 +4,7 @@
 //   status[n]        uint32 level / distance, 0xFFFFFFFF = not reached
 //   bitmap[n/32]     BFS visited bits (claimed with atomicOr)
 //   epoch[n]         SSSP stamp of the iteration that last queued a vertex
-//   node lists x2    worklist entries {v int32, beg int64, scan int64} plus
+//   node lists x2    worklist entries {v, beg, scan: int32 each} plus
 //                    tstart[] (first entry of every WD tile); double-buffered
 //   sub lists x2     HP sub-worklists, same layout
 //   edge lists x2    EP worklists of CSR edge ids (COO edge index = CSR index)
@@ -97,10 +97,12 @@ struct GraphDev {
     int64_t m;
 };
 
+// Worklist entries.  Edge indices and list prefixes are below m < 2^31, so
+// they are stored in 32 bits (half the bytes, single-instruction shuffles).
 struct NodeList {
     int32_t *v;
-    int64_t *beg;
-    int64_t *scan;    // exclusive prefix of entry lengths; scan[cnt] = total
+    int32_t *beg;     // first CSR edge of the entry
+    int32_t *scan;    // exclusive prefix of entry lengths; scan[cnt] = total
     int32_t *tstart;  // tstart[k]: entry holding list edge k * tile
 };
 

@@ -10,7 +10,7 @@
 // state) in one fixed-size array of device memory declared in this file.
 // Each GPU that loads the library holds that array until the process exits.
 //
-// Limits: n <= 131072 vertices and m <= 16777216 edges (about 5.9 MiB of
+// Limits: n <= 131072 vertices and m <= 16777216 edges (about 3.6 MiB of
 // scratch).  Every call on a device shares the array and finds the previous
 // call's contents in it; the kernels reset what must start at zero (loop
 // counters, the visited bitmap and the output levels).  Calls whose work
@@ -38,8 +38,8 @@ constexpr size_t kOffCtl = 0;
 constexpr size_t kOffBitmap = align256(kOffCtl + sizeof(Ctl));
 constexpr size_t kOffEpoch = align256(kOffBitmap + sizeof(uint32_t) * (size_t)((kNaMaxN + 31) / 32));
 constexpr size_t kListV = align256(sizeof(int32_t) * (size_t)kNaMaxN);
-constexpr size_t kListBeg = align256(sizeof(int64_t) * (size_t)kNaMaxN);
-constexpr size_t kListScan = align256(sizeof(int64_t) * (size_t)(kNaMaxN + 1));
+constexpr size_t kListBeg = align256(sizeof(int32_t) * (size_t)kNaMaxN);
+constexpr size_t kListScan = align256(sizeof(int32_t) * (size_t)(kNaMaxN + 1));
 constexpr size_t kListTiles = align256(sizeof(int32_t) * (size_t)kNaTiles);
 constexpr size_t kListBytes = kListV + kListBeg + kListScan + kListTiles;
 constexpr size_t kOffLists = align256(kOffEpoch + sizeof(uint32_t));  // BFS needs no stamps
@@ -104,8 +104,8 @@ extern "C" lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t
     for (int b = 0; b < 2; ++b) {
         unsigned char *L = base + kOffLists + (size_t)b * kListBytes;
         p.lists[b].v = (int32_t *)L;
-        p.lists[b].beg = (int64_t *)(L + kListV);
-        p.lists[b].scan = (int64_t *)(L + kListV + kListBeg);
+        p.lists[b].beg = (int32_t *)(L + kListV);
+        p.lists[b].scan = (int32_t *)(L + kListV + kListBeg);
         p.lists[b].tstart = (int32_t *)(L + kListV + kListBeg + kListScan);
     }
     p.list_cap = n;

@@ -30,14 +30,14 @@
 #include <thread>
 #include <vector>
 
-#include "lb_device.cuh"
+#include "lb_steps.cuh"
 
 namespace lbk {
 namespace srv {
 
 constexpr uint32_t kRing = 1u << 16;         // request / completion ring entries
 constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
-constexpr int kItems = 4;
+constexpr int kItems = 2;
 
 enum : uint32_t { kJobNone = 0, kJobInit = 1, kJobRelax = 2, kJobCheck = 3 };
 
@@ -146,7 +146,7 @@ __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned l
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ int64_t list_search_cg(const int64_t *scan, int64_t lo, int64_t hi, int64_t e) {
+__device__ __forceinline__ int64_t list_search_cg(const int32_t *scan, int64_t lo, int64_t hi, int64_t e) {
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
         if (__ldcg(scan + mid) <= e) lo = mid; else hi = mid;
@@ -265,9 +265,9 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
         }
         NodeList L = S->lists[0];
         L.v[0] = st.src;
-        L.beg[0] = beg;
+        L.beg[0] = (int32_t)beg;
         L.scan[0] = 0;
-        L.scan[1] = deg;
+        L.scan[1] = (int32_t)deg;
         const int64_t grains = (deg + kTileGrain - 1) / kTileGrain;
         for (int64_t k = 0; k < grains && k < P.tile_cap; ++k) L.tstart[k] = 0;
         S->in_cnt = 1;
@@ -286,7 +286,7 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
         const uint32_t out = st.par ^ 1u;
         const uint32_t err = atomicOr(&S->error, 0u);
         if (cnt > 0 && st.level + 1 <= (uint32_t)g.n && !(err & (kErrCapacity | kErrBounds))) {
-            S->lists[out].scan[cnt] = edges;
+            S->lists[out].scan[cnt] = (int32_t)edges;
             S->par = out;
             S->in_cnt = (uint32_t)cnt;
             S->in_edges = (uint64_t)edges;
@@ -341,15 +341,9 @@ template <bool SSSP>
 __device__ void relax_tile(const Params &P, Slot *S, int64_t t, WarpBuf &wb, WarpScratch &ws) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
-    const uint32_t par = st.par;
-    const int64_t in_cnt = st.in_cnt;
-    const int64_t E = (int64_t)st.in_edges;
-    const uint32_t level = st.level;
-    const uint32_t stamp = st.epoch_base + level;
-    uint32_t *status = st.status;
-    const NodeList in = S->lists[par];
+    const int64_t q = ((const volatile Slot *)S)->job_q;
     FlushOut o;
-    o.list = S->lists[par ^ 1u];
+    o.list = S->lists[st.par ^ 1u];
     o.elist = nullptr;
     o.pack = &S->out_pack;
     o.cap = P.slot_cap;
@@ -358,63 +352,11 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, WarpBuf &wb, War
     o.mdt = 1;
     o.err = &S->error;
     o.pushes = &S->pushes;
-    const int64_t q = ((const volatile Slot *)S)->job_q;
-    const int64_t T = q * kTileGrain;
-    const int64_t ntiles = (E + T - 1) / T;
-    const int64_t e0 = t * T;
-    const int64_t e1 = min(e0 + T, E);
-    int64_t i0 = __ldcg(in.tstart + t * q);
-    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldcg(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
-    if (i0 < 0 || i0 >= ihi) {
-        if (threadIdx.x == 0) atomicOr(&S->error, kErrBounds);
-        return;
-    }
+    o.child_first = nullptr;
     uint32_t cnt = 0;
-    for (int64_t r0 = e0; r0 < e1; r0 += (int64_t)kBlock * kItems) {
-        int32_t vv[kItems];
-        uint32_t ww[kItems], dd[kItems];
-        bool ok[kItems];
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            const int64_t e = r0 + (int64_t)it * kBlock + threadIdx.x;
-            ok[it] = false;
-            vv[it] = 0;
-            ww[it] = 0;
-            dd[it] = 0;
-            if (e < e1) {
-                const int64_t k = list_search_cg(in.scan, i0, ihi, e);
-                const int64_t eidx = __ldcg(in.beg + k) + (e - __ldcg(in.scan + k));
-                if ((uint64_t)eidx >= (uint64_t)g.m) {
-                    atomicOr(&S->error, kErrBounds);
-                } else {
-                    ok[it] = true;
-                    vv[it] = __ldg(g.col + eidx);
-                    if (SSSP) {
-                        ww[it] = __ldg(g.w + eidx);
-                        const int32_t u = __ldcg(in.v + k);
-                        dd[it] = __ldcg(S->epoch + u) == stamp ? kInf : __ldcg(status + u);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            bool want = false;
-            int64_t vb = 0;
-            uint32_t vd = 0;
-            if (ok[it]) {
-                const bool hit = SSSP ? sssp_relax_cg(status, S->epoch, vv[it], dd[it], ww[it], stamp, &S->error)
-                                      : bfs_claim_cg(S->bitmap, status, vv[it], level + 1);
-                if (hit) {
-                    vb = __ldg(g.off + vv[it]);
-                    vd = (uint32_t)(__ldg(g.off + vv[it] + 1) - vb);
-                    want = vd > 0;
-                }
-            }
-            wpush(wb, cnt, want, vv[it], vb, vd);
-            if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o);
-        }
-    }
+    wd_walk_tile<SSSP, kItems, true>(g, S->lists[st.par], st.in_cnt, (int64_t)st.in_edges, q * kTileGrain, t,
+                                     S->bitmap, S->epoch, st.status, st.level, st.epoch_base + st.level, &S->error, wb,
+                                     ws, cnt, o);
     wflush<kOutNode, true>(wb, ws, cnt, o);
 }
 
@@ -473,7 +415,7 @@ __device__ void admit(const Params &P) {
 
 // ---- the persistent kernel -------------------------------------------------
 
-__global__ void __launch_bounds__(kBlock) k_serve(Params P) {
+__global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
     __shared__ int s_slot;
@@ -484,6 +426,10 @@ __global__ void __launch_bounds__(kBlock) k_serve(Params P) {
     uint64_t idle_since = 0;
     uint32_t scan_from = blockIdx.x % (uint32_t)P.nslots;
     for (;;) {
+        // every thread has read the previous iteration's s_* values before
+        // thread 0 overwrites them (without this barrier a lagging warp could
+        // pick up the next tile out of step with its block)
+        __syncthreads();
         if (threadIdx.x == 0) {
             s_slot = -1;
             s_exit = 0;
@@ -560,7 +506,6 @@ __global__ void __launch_bounds__(kBlock) k_serve(Params P) {
                 finish_job(P, S, kind);
             }
         }
-        __syncthreads();
     }
 }
 
@@ -737,7 +682,7 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     s->slot_cap = s->slot_n;
     s->tile_cap = s->slot_m / kTileGrain + 2;
     // per slot: bitmap + stamps + two worklists (v, beg, scan, tile starts)
-    const int64_t per_list = 4 * s->slot_cap + 8 * s->slot_cap + 8 * (s->slot_cap + 1) + 4 * s->tile_cap;
+    const int64_t per_list = 4 * s->slot_cap + 4 * s->slot_cap + 4 * (s->slot_cap + 1) + 4 * s->tile_cap;
     s->slot_bytes = 4 * ((s->slot_n + 31) / 32) + 4 * s->slot_n + 2 * per_list + 4096;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -779,8 +724,8 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
         if (e == cudaSuccess) e = cudaMemset(S.epoch, 0, 4 * (size_t)s->slot_n);
         for (int b = 0; b < 2; ++b) {
             get((void **)&S.lists[b].v, 4 * (size_t)s->slot_cap);
-            get((void **)&S.lists[b].beg, 8 * (size_t)s->slot_cap);
-            get((void **)&S.lists[b].scan, 8 * (size_t)(s->slot_cap + 1));
+            get((void **)&S.lists[b].beg, 4 * (size_t)s->slot_cap);
+            get((void **)&S.lists[b].scan, 4 * (size_t)(s->slot_cap + 1));
             get((void **)&S.lists[b].tstart, 4 * (size_t)s->tile_cap);
         }
     }

@@ -205,91 +205,112 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
 // its prefix / first edge come from the loading lane by shuffle.  That
 // replaces a per-edge search (the bulk of the instructions) by a few
 // warp-wide operations per 32 edges.
-template <bool SSSP, int STEPS>
-__device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt, int64_t E,
-                                        WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
-                                        uint32_t *status, uint32_t level, uint32_t stamp) {
-    const int64_t T = iteration_tile(E, gridDim.x, p.tile);
+template <bool COH, class T>
+__device__ __forceinline__ T ld_list(const T *p) {
+    return COH ? __ldcg(p) : __ldg(p);
+}
+
+// One tile of the walk.  COH selects L2-coherent loads for everything other
+// CTAs write (the persistent serving kernel); the single-query launches use
+// the read-only / L1 paths.
+template <bool SSSP, int STEPS, bool COH>
+__device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
+                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
+                                             uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
+                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
     const int64_t q = T / kTileGrain;
     const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
     const int64_t ntiles = (E + T - 1) / T;
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
     const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t e0 = t * T;
-        const int64_t e1 = min(e0 + T, E);
-        int64_t i0 = __ldg(in.tstart + t * q);
-        int64_t ihi = (t + 1 < ntiles) ? min((int64_t)__ldg(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
-        if (i0 < 0 || i0 >= ihi) {
-            if (lane == 0) atomicOr(&ctl->error, kErrBounds);
-            i0 = 0;
-            ihi = in_cnt;
-        }
-        const int64_t w0 = e0 + (int64_t)warp * W;
-        const int64_t w1 = min(w0 + W, e1);
-        if (w0 >= w1) continue;  // warp-uniform
-        int64_t kcur = list_search(in.scan, i0, ihi, w0);
-        int64_t scur = __ldg(in.scan + kcur);
-        int64_t bcur = __ldg(in.beg + kcur);
-        int32_t ucur = SSSP ? __ldg(in.v + kcur) : 0;
-        for (int64_t ew = w0; ew < w1; ew += 32 * STEPS) {
-            int32_t vv[STEPS];
-            uint32_t ww[STEPS], dd[STEPS];
-            bool ok[STEPS];
+    const int64_t e0 = t * T;
+    const int64_t e1 = min(e0 + T, E);
+    int64_t i0 = ld_list<COH>(in.tstart + t * q);
+    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)ld_list<COH>(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
+    if (i0 < 0 || i0 >= ihi) {
+        if (lane == 0) atomicOr(err, kErrBounds);
+        return;
+    }
+    const int64_t w0 = e0 + (int64_t)warp * W;
+    const int64_t w1 = min(w0 + W, e1);
+    if (w0 >= w1) return;  // warp-uniform
+    int64_t lo = i0, hi = ihi;  // entry of the slice's first edge
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
+    }
+    int64_t kcur = lo;
+    int32_t scur = ld_list<COH>(in.scan + kcur);
+    int32_t bcur = ld_list<COH>(in.beg + kcur);
+    int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
+    for (int64_t ew = w0; ew < w1; ew += 32 * STEPS) {
+        int32_t vv[STEPS];
+        uint32_t ww[STEPS], dd[STEPS];
+        bool ok[STEPS];
 #pragma unroll
-            for (int st = 0; st < STEPS; ++st) {
-                const int64_t es = ew + 32 * st;  // first edge of this step (uniform)
-                const int64_t e = es + lane;
-                ok[st] = false;
-                vv[st] = 0;
-                ww[st] = 0;
-                dd[st] = 0;
-                if (es >= w1) continue;  // warp-uniform
-                const int64_t j = kcur + 1 + lane;
-                int64_t sj = INT64_MAX, bj = 0;
-                int32_t uj = 0;
-                if (j < ihi) {
-                    sj = __ldg(in.scan + j);
-                    bj = __ldg(in.beg + j);
-                    if (SSSP) uj = __ldg(in.v + j);
-                }
-                const int64_t pos = sj - es;  // >= 1: entry j starts after es
-                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
-                const int c = __popc(starts & upto);
-                const int src_lane = c > 0 ? c - 1 : 0;
-                const int64_t s_sh = __shfl_sync(kFull, sj, src_lane);
-                const int64_t b_sh = __shfl_sync(kFull, bj, src_lane);
-                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
-                const int64_t s_l = c > 0 ? s_sh : scur;
-                const int64_t b_l = c > 0 ? b_sh : bcur;
-                const int32_t u_l = c > 0 ? u_sh : ucur;  // taken before the walk advances
-                // advance to the entry holding the next step's first edge
-                const int adv = __popc(__ballot_sync(kFull, sj <= es + 32));
-                if (adv > 0) {
-                    scur = __shfl_sync(kFull, sj, adv - 1);
-                    bcur = __shfl_sync(kFull, bj, adv - 1);
-                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
-                    kcur += adv;
-                }
-                if (e < w1) {
-                    const int64_t eidx = b_l + (e - s_l);
-                    if ((uint64_t)eidx >= (uint64_t)p.g.m) {
-                        atomicOr(&ctl->error, kErrBounds);
-                    } else {
-                        ok[st] = true;
-                        vv[st] = __ldg(p.g.col + eidx);
-                        if (SSSP) {
-                            ww[st] = __ldg(p.g.w + eidx);
-                            dd[st] = sssp_source_dist(status, p.epoch, u_l, stamp);
-                        }
+        for (int st = 0; st < STEPS; ++st) {
+            const int64_t es = ew + 32 * st;  // first edge of this step (uniform)
+            const int64_t e = es + lane;
+            ok[st] = false;
+            vv[st] = 0;
+            ww[st] = 0;
+            dd[st] = 0;
+            if (es >= w1) continue;  // warp-uniform
+            const int64_t j = kcur + 1 + lane;
+            int32_t sj = INT32_MAX, bj = 0;
+            int32_t uj = 0;
+            if (j < ihi) {
+                sj = ld_list<COH>(in.scan + j);
+                bj = ld_list<COH>(in.beg + j);
+                if (SSSP) uj = ld_list<COH>(in.v + j);
+            }
+            const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
+            const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
+            const int c = __popc(starts & upto);
+            const int src_lane = c > 0 ? c - 1 : 0;
+            const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
+            const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
+            const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
+            const int32_t s_l = c > 0 ? s_sh : scur;
+            const int32_t b_l = c > 0 ? b_sh : bcur;
+            const int32_t u_l = c > 0 ? u_sh : ucur;  // taken before the walk advances
+            // advance to the entry holding the next step's first edge
+            const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
+            if (adv > 0) {
+                scur = __shfl_sync(kFull, sj, adv - 1);
+                bcur = __shfl_sync(kFull, bj, adv - 1);
+                if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
+                kcur += adv;
+            }
+            if (e < w1) {
+                const int64_t eidx = (int64_t)b_l + (e - (int64_t)s_l);
+                if ((uint64_t)eidx >= (uint64_t)g.m) {
+                    atomicOr(err, kErrBounds);
+                } else {
+                    ok[st] = true;
+                    vv[st] = __ldg(g.col + eidx);
+                    if (SSSP) {
+                        ww[st] = __ldg(g.w + eidx);
+                        dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
                     }
                 }
             }
-            relax_items<SSSP, STEPS, kOutNode, true>(ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status, level, stamp,
-                                                     &ctl->error, wb, ws, cnt, o);
         }
+        relax_items<SSSP, STEPS, kOutNode, true, COH>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
+                                                      err, wb, ws, cnt, o);
     }
+}
+
+template <bool SSSP, int STEPS>
+__device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt, int64_t E,
+                                        WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
+                                        uint32_t *status, uint32_t level, uint32_t stamp) {
+    const int64_t T = iteration_tile(E, gridDim.x, p.tile);
+    const int64_t ntiles = (E + T - 1) / T;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+        wd_walk_tile<SSSP, STEPS, false>(p.g, in, in_cnt, E, T, t, p.bitmap, p.epoch, status, level, stamp,
+                                         &ctl->error, wb, ws, cnt, o);
 }
 
 template <bool SSSP, int ITEMS>
@@ -409,7 +430,7 @@ __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
     const int64_t thr = p.hp_threshold;
     if (kind == 1u && sub_cnt > 0) {
         const uint32_t so = ctl->hp_from == kHpFromSuper ? 0u : (ctl->sub_in ^ 1u);
-        p.subs[so].scan[sub_cnt] = sub_edges;
+        p.subs[so].scan[sub_cnt] = (int32_t)sub_edges;
         ctl->hp_from = kHpFromSub;
         ctl->sub_in = so;
         ctl->in_cnt = (uint32_t)sub_cnt;
@@ -423,7 +444,7 @@ __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
         const int64_t edges = (int64_t)(pk & 0xFFFFFFFFull);
         if (cnt > p.list_cap) { ctl->error |= kErrCapacity; cnt = p.list_cap; }
         const uint32_t out = ctl->par ^ 1u;
-        p.lists[out].scan[cnt] = edges;
+        p.lists[out].scan[cnt] = (int32_t)edges;
         ctl->par = out;
         ctl->in_cnt = (uint32_t)cnt;
         ctl->in_edges = (uint64_t)edges;

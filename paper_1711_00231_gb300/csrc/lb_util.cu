@@ -123,17 +123,17 @@ __global__ void k_init(StepParams p) {
         const int32_t cf = p.strategy == LB_NS_PHYS ? p.child_first[src] : -1;
         for (int64_t j = tid; j < units; j += stride) {
             L.v[j] = (cf >= 0 && j > 0) ? cf + (int32_t)(j - 1) : src;
-            L.beg[j] = beg + j * p.mdt;
-            L.scan[j] = j * p.mdt;
+            L.beg[j] = (int32_t)(beg + j * p.mdt);
+            L.scan[j] = (int32_t)(j * p.mdt);
         }
-        if (tid == 0) L.scan[units] = deg;
+        if (tid == 0) L.scan[units] = (int32_t)deg;
         return;
     }
     if (tid == 0) {
         L.v[0] = src;
-        L.beg[0] = beg;
+        L.beg[0] = (int32_t)beg;
         L.scan[0] = 0;
-        L.scan[deg > 0 ? 1 : 0] = deg;
+        L.scan[deg > 0 ? 1 : 0] = (int32_t)deg;
     }
     if (L.tstart != nullptr) {
         const int64_t tiles = (deg + kTileGrain - 1) / kTileGrain;
@@ -443,7 +443,7 @@ __global__ void k_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList 
         if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, o);
     }
     wflush<kOutNode, true>(wb, ws, cnt, o);
-    if (lane == 0) list.scan[F] = E;
+    if (lane == 0) list.scan[F] = (int32_t)E;
 }
 
 cudaError_t launch_wd_offsets(const int64_t *deg, int64_t F, int64_t T, NodeList list, Ctl *ctl, int64_t *ept_out,

@@ -343,7 +343,7 @@ def test_ns_phys_matches_paper_example_and_reports_memory():
         children = oracle.ns_split(g.offsets, 4)[0]
         assert rep["ns_children"] == children == 2
         assert rep["ns_split"] == 4 * g.n + 8 * children
-        assert rep["node_lists"] == 2 * 20 * (g.n + children) + 16
+        assert rep["node_lists"] == 2 * 12 * (g.n + children) + 8
     finally:
         G.close()
 
