@@ -497,6 +497,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
         else if (kind == kJobCheck) check_tile(P, S, s_tile);
         else if (((const volatile Slot *)S)->kind == 1) relax_tile<true>(P, S, s_tile, s_wb[warp], s_ws[warp]);
         else relax_tile<false>(P, S, s_tile, s_wb[warp], s_ws[warp]);
+        // Other CTAs read this tile's stores (list entries, resets) in the
+        // slot's next job within this same kernel: every thread makes its own
+        // stores visible device-wide before the tile is counted as done.
+        __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();

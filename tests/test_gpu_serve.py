@@ -117,6 +117,27 @@ def test_continuous_arrivals_and_relaunch(mix):
         S.close()
 
 
+def test_many_small_rounds_with_few_slots(mix):
+    # two slots, a short idle timeout and a steady trickle: the persistent
+    # kernel keeps finding no work between requests, leaves, and is
+    # relaunched many times; every result must still be exact
+    import torch
+    graphs, handles = mix
+    S = sv.Server(handles, slots=2, idle_us=50, tile=256)
+    try:
+        reqs = make_requests(graphs, 120, seed=21)
+        for i, r in enumerate(reqs):
+            r.arrival_s = 0.0005 * i
+        outs = [torch.empty(graphs[r.graph].n, dtype=torch.int32, device="cuda") for r in reqs]
+        res = sv.serve(S, reqs, outs, timeout_s=120)
+        assert res["statuses_ok"]
+        torch.cuda.synchronize()
+        for r, o in zip(reqs, outs):
+            assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src))
+    finally:
+        S.close()
+
+
 def test_overflow_and_invalid_requests(mix):
     import torch
     graphs, handles = mix
