@@ -236,6 +236,42 @@ def chunking_ablation(torch, sources: int = 4):
     return row
 
 
+def grid_bench(torch):
+    """The high-diameter configuration: SSSP (and BFS) from a corner of a
+    4096 x 4096 grid (weights U[1,1000]): thousands of small iterations, so
+    per-iteration overhead dominates.  Single-query device loop vs the same
+    query through the persistent engine."""
+    import graphgen as gg
+    from paper_1711_00231_gb300 import lb
+    from paper_1711_00231_gb300 import serve as sv
+    g = gg.grid(4096, 4096, seed=1)
+    G = lb.Graph.from_csr(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    row = {"graph": "4096 x 4096 grid, 4-neighbour, weights U[1,1000], source = corner"}
+    for kind in ("bfs", "sssp"):
+        (G.bfs_dev if kind == "bfs" else G.sssp_dev)(0, "WD", out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        (G.bfs_dev if kind == "bfs" else G.sssp_dev)(0, "WD", out)
+        b.record()
+        torch.cuda.synchronize()
+        st = G.stats()
+        row[f"{kind}_ms"] = a.elapsed_time(b)
+        row[f"{kind}_iterations"] = st["iterations"]
+        row[f"{kind}_us_per_iteration"] = 1e3 * a.elapsed_time(b) / max(1, st["iterations"])
+        row[f"{kind}_gteps"] = g.m / (a.elapsed_time(b) / 1e3) / 1e9
+    S = sv.Server([G], slots=4)
+    for kind in ("bfs", "sssp"):
+        S.run_batch([sv.Request(0.0, 0, 0, kind)], [out])
+        t0 = time.perf_counter()
+        S.run_batch([sv.Request(0.0, 0, 0, kind)], [out])
+        row[f"{kind}_server_ms"] = 1e3 * (time.perf_counter() - t0)
+    S.close()
+    G.close()
+    return row
+
+
 def serving_mix(seed: int = 1):
     """The resident graph mix of the serving workload: 24 R-MAT graphs
     (scale 12..20, edge factor 8/16/32, drawn with `seed`) and 8 grids
@@ -485,6 +521,7 @@ def main():
             extra[kind] = row
         G.release()
         extra["chunking_ablation"] = chunking_ablation(torch)
+        extra["grid4096"] = grid_bench(torch)
 
     # end to end through the host-buffer C-ABI calls (lb_bfs / lb_sssp):
     # includes the D2H copy of every result into pinned host memory

@@ -365,7 +365,7 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, WarpBuf &wb, War
 __device__ void admit(const Params &P) {
     Shared *sh = P.sh;
     const unsigned long long sub = ld_acquire_sys(&P.host->submitted);
-    unsigned long long con = sh->consumed;
+    unsigned long long con = __ldcg(&sh->consumed);  // written by whichever CTA held the lock last
     int32_t cursor = 0;
     while (con < sub) {
         Slot *S = nullptr;
@@ -375,7 +375,13 @@ __device__ void admit(const Params &P) {
                 break;
             }
         if (!S) break;
-        const Req r = P.host->req[con % kRing];
+        const volatile Req *vr = &P.host->req[con % kRing];  // host memory, written by the host
+        Req r;
+        r.graph = vr->graph;
+        r.src = vr->src;
+        r.kind = vr->kind;
+        r.out = vr->out;
+        r.ticket = vr->ticket;
         S->ticket = r.ticket;
         S->graph = r.graph;
         S->src = r.src;
@@ -430,42 +436,74 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
         // thread 0 overwrites them (without this barrier a lagging warp could
         // pick up the next tile out of step with its block)
         __syncthreads();
-        if (threadIdx.x == 0) {
-            s_slot = -1;
-            s_exit = 0;
-            for (int32_t c = 0; c < P.nslots; ++c) {
+        if (threadIdx.x < 32) {
+            // warp 0 looks at 32 slots per round: each lane reads one slot's
+            // claim word and job fields, and the claimable slots are tried in
+            // order until a claim holds (one L2 round trip per 32 slots)
+            const uint32_t lane = threadIdx.x;
+            int found = -1;
+            uint32_t f_kind = 0, f_tiles = 0, f_tile = 0;
+            for (int32_t c0 = 0; c0 < P.nslots && found < 0; c0 += 32) {
+                const int32_t c = c0 + (int32_t)lane;
                 const int32_t si = (int32_t)((scan_from + (uint32_t)c) % (uint32_t)P.nslots);
-                Slot *S = &P.slots[si];
-                const unsigned long long w = __ldcg(&S->claim);
-                const uint32_t kind = __ldcg(&S->job_kind);
-                const uint32_t tiles = __ldcg(&S->job_tiles);
-                if (kind == kJobNone || (uint32_t)w >= tiles) continue;
-                const unsigned long long old = atomicAdd(&S->claim, 1ull);
-                __threadfence();
-                // the claim counts only if the job fields still belong to the
-                // generation it was taken in (a late claim on a finished job
-                // must not take a tile of the slot's next job)
-                const uint32_t g2 = __ldcg(&S->job_gen);
-                const uint32_t k2 = __ldcg(&S->job_kind);
-                const uint32_t t2 = __ldcg(&S->job_tiles);
-                if (g2 == (uint32_t)(old >> 32) && k2 != kJobNone && (uint32_t)old < t2) {
-                    s_slot = si;
-                    s_kind = k2;
-                    s_tiles = t2;
-                    s_tile = (long long)(uint32_t)old;
-                    scan_from = (uint32_t)si;
-                    break;
+                bool claimable = false;
+                if (c < P.nslots) {
+                    const Slot *S = &P.slots[si];
+                    const unsigned long long w = __ldcg(&S->claim);
+                    const uint32_t kind = __ldcg(&S->job_kind);
+                    const uint32_t tiles = __ldcg(&S->job_tiles);
+                    claimable = kind != kJobNone && (uint32_t)w < tiles;
+                }
+                unsigned cand = __ballot_sync(kFull, claimable);
+                while (cand) {
+                    const int l = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    int ok = 0;
+                    uint32_t k2 = 0, t2 = 0, idx = 0;
+                    if ((int)lane == l) {
+                        Slot *S = &P.slots[si];
+                        const unsigned long long old = atomicAdd(&S->claim, 1ull);
+                        __threadfence();
+                        // the claim counts only if the job fields still belong to
+                        // the generation it was taken in (a late claim on a
+                        // finished job must not take a tile of the next job)
+                        const uint32_t g2 = __ldcg(&S->job_gen);
+                        k2 = __ldcg(&S->job_kind);
+                        t2 = __ldcg(&S->job_tiles);
+                        idx = (uint32_t)old;
+                        ok = g2 == (uint32_t)(old >> 32) && k2 != kJobNone && idx < t2;
+                    }
+                    ok = __shfl_sync(kFull, ok, l);
+                    if (ok) {
+                        found = __shfl_sync(kFull, si, l);
+                        f_kind = __shfl_sync(kFull, k2, l);
+                        f_tiles = __shfl_sync(kFull, t2, l);
+                        f_tile = __shfl_sync(kFull, idx, l);
+                        break;
+                    }
                 }
             }
+            if (found >= 0) scan_from = (uint32_t)found;  // every lane keeps the same start
+            if (lane == 0) {
+                s_slot = found;
+                s_exit = 0;
+                if (found >= 0) {
+                    s_kind = f_kind;
+                    s_tiles = f_tiles;
+                    s_tile = (long long)f_tile;
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
             if (s_slot < 0) {
                 const uint64_t now = global_ns();
                 // Admission and the decision to stop are taken under one lock,
                 // so no request is admitted after the grid decided to leave.
                 if (atomicCAS(&P.sh->admit_lock, 0u, 1u) == 0u) {
                     if (__ldcg(&P.sh->stopping) == 0u) {
-                        const unsigned long long before = P.sh->consumed;
+                        const unsigned long long before = __ldcg(&P.sh->consumed);
                         admit(P);
-                        const bool admitted = P.sh->consumed != before;
+                        const bool admitted = __ldcg(&P.sh->consumed) != before;
                         if (admitted || __ldcg(&P.sh->active) != 0u) {
                             idle_since = 0;
                         } else if (idle_since == 0) {
