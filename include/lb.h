@@ -295,6 +295,27 @@ lb_status lb_server_submit(lb_server *s, int32_t graph, int32_t src, int32_t kin
  * and relaunches the persistent kernel if work is pending and it has left. */
 lb_status lb_server_poll(lb_server *s, lb_completion *out, int32_t cap, int32_t *ndone);
 
+/* Diagnostic snapshot of the engine (read while it runs): host and device
+ * counters, and the first 16 busy slots with their current job. */
+typedef struct lb_slot_state_t {
+    int32_t slot, graph, kind, level;
+    int32_t job_kind;   /* 0 none, 1 reset, 2 relax, 3 overflow check */
+    int32_t job_tiles, job_done, job_gen;
+    int64_t claim;      /* generation << 32 | next tile */
+    int64_t in_cnt, in_edges;
+    int32_t error, pad;
+    int64_t ticket;
+} lb_slot_state_t;
+
+typedef struct lb_server_state_t {
+    int64_t submitted, consumed, completed, acked;
+    int32_t active, stopping, admit_lock, kernel_error;
+    int32_t kernel_running, busy_slots, listed, pad;
+    lb_slot_state_t slot[16];
+} lb_server_state_t;
+
+lb_status lb_server_state(lb_server *s, lb_server_state_t *out);
+
 /* Asks the persistent kernel to leave and waits for it (queries in flight
  * stay in their slots and resume at the next submit / poll). */
 lb_status lb_server_stop(lb_server *s);

@@ -71,12 +71,25 @@ struct HostShared {
     Done done[kRing];
 };
 
+// The open job is described by ONE 64-bit word, so that a claimer reads
+// generation, kind, tile size and tile count in a single load: with separate
+// fields a late claimer could pair an old generation with a new tile count
+// and take a tile of the next job twice.
+//   bits 63..32 generation, 31..30 kind, 29..24 q (RELAX tile = q * 256
+//   edges, q <= 32), 23..0 tiles (RELAX tiles < 2^31 / 256, INIT and CHECK
+//   tiles < 2^31 / 2^16)
+__host__ __device__ constexpr unsigned long long job_word(uint32_t gen, uint32_t kind, uint32_t q, uint32_t tiles) {
+    return (unsigned long long)gen << 32 | (unsigned long long)(kind & 3u) << 30 |
+           (unsigned long long)(q & 63u) << 24 | (unsigned long long)(tiles & 0xFFFFFFu);
+}
+__host__ __device__ constexpr uint32_t job_gen(unsigned long long w) { return (uint32_t)(w >> 32); }
+__host__ __device__ constexpr uint32_t job_kind(unsigned long long w) { return (uint32_t)(w >> 30) & 3u; }
+__host__ __device__ constexpr uint32_t job_q(unsigned long long w) { return (uint32_t)(w >> 24) & 63u; }
+__host__ __device__ constexpr uint32_t job_tiles(unsigned long long w) { return (uint32_t)w & 0xFFFFFFu; }
+
 struct Slot {
     unsigned long long claim;  // generation << 32 | next tile
-    uint32_t job_gen;          // generation the job fields below belong to
-    uint32_t job_q;            // RELAX: tile = job_q * kTileGrain edges
-    uint32_t job_kind;
-    uint32_t job_tiles;
+    unsigned long long job;    // job_word(generation, kind, q, tiles)
     uint32_t job_done;
     uint32_t busy;
     int32_t graph;
@@ -208,11 +221,9 @@ __device__ __forceinline__ SlotState slot_state(const Slot *S) {
 __device__ void open_job(Slot *S, uint32_t kind, uint32_t tiles, uint32_t q = 1) {
     const unsigned long long w = atomicAdd(&S->claim, 0ull);
     const uint32_t gen = (uint32_t)(w >> 32) + 1u;
-    S->job_gen = gen;
-    S->job_q = q;
-    S->job_kind = kind;
-    S->job_tiles = tiles;
     S->job_done = 0;
+    __threadfence();
+    atomicExch(&S->job, job_word(gen, kind, q, tiles));
     __threadfence();
     atomicExch(&S->claim, (unsigned long long)gen << 32);
 }
@@ -231,8 +242,8 @@ __device__ void complete_query(const Params &P, Slot *S, int32_t status_code) {
     __threadfence_system();
     st_release_sys(&d->seq, idx + 1ull);
     S->epoch_next = V->epoch_base + V->level + 1;
-    S->job_kind = kJobNone;
-    S->job_tiles = 0;
+    const unsigned long long jw = atomicAdd(&S->job, 0ull);
+    atomicExch(&S->job, job_word(job_gen(jw), kJobNone, 0u, 0u));
     __threadfence();
     S->busy = 0;
     atomicSub(&P.sh->active, 1u);
@@ -338,10 +349,9 @@ __device__ void check_tile(const Params &P, Slot *S, int64_t k) {
 }
 
 template <bool SSSP>
-__device__ void relax_tile(const Params &P, Slot *S, int64_t t, WarpBuf &wb, WarpScratch &ws) {
+__device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t q, WarpBuf &wb, WarpScratch &ws) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
-    const int64_t q = ((const volatile Slot *)S)->job_q;
     FlushOut o;
     o.list = S->lists[st.par ^ 1u];
     o.elist = nullptr;
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
     __shared__ int s_slot;
-    __shared__ uint32_t s_kind, s_tiles;
+    __shared__ uint32_t s_kind, s_tiles, s_q;
     __shared__ long long s_tile;
     __shared__ int s_exit;
     const uint32_t warp = threadIdx.x >> 5;
@@ -442,7 +452,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
             // order until a claim holds (one L2 round trip per 32 slots)
             const uint32_t lane = threadIdx.x;
             int found = -1;
-            uint32_t f_kind = 0, f_tiles = 0, f_tile = 0;
+            uint32_t f_kind = 0, f_tiles = 0, f_tile = 0, f_q = 0;
             for (int32_t c0 = 0; c0 < P.nslots && found < 0; c0 += 32) {
                 const int32_t c = c0 + (int32_t)lane;
                 const int32_t si = (int32_t)((scan_from + (uint32_t)c) % (uint32_t)P.nslots);
@@ -450,34 +460,36 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
                 if (c < P.nslots) {
                     const Slot *S = &P.slots[si];
                     const unsigned long long w = __ldcg(&S->claim);
-                    const uint32_t kind = __ldcg(&S->job_kind);
-                    const uint32_t tiles = __ldcg(&S->job_tiles);
-                    claimable = kind != kJobNone && (uint32_t)w < tiles;
+                    const unsigned long long jw = __ldcg(&S->job);
+                    claimable = job_kind(jw) != kJobNone && job_gen(jw) == (uint32_t)(w >> 32) &&
+                                (uint32_t)w < job_tiles(jw);
                 }
                 unsigned cand = __ballot_sync(kFull, claimable);
                 while (cand) {
                     const int l = __ffs(cand) - 1;
                     cand &= cand - 1;
                     int ok = 0;
-                    uint32_t k2 = 0, t2 = 0, idx = 0;
+                    uint32_t k2 = 0, t2 = 0, q2 = 0, idx = 0;
                     if ((int)lane == l) {
                         Slot *S = &P.slots[si];
                         const unsigned long long old = atomicAdd(&S->claim, 1ull);
                         __threadfence();
-                        // the claim counts only if the job fields still belong to
+                        // the claim counts only if the job word still belongs to
                         // the generation it was taken in (a late claim on a
                         // finished job must not take a tile of the next job)
-                        const uint32_t g2 = __ldcg(&S->job_gen);
-                        k2 = __ldcg(&S->job_kind);
-                        t2 = __ldcg(&S->job_tiles);
+                        const unsigned long long jw = atomicAdd(&S->job, 0ull);
+                        k2 = job_kind(jw);
+                        t2 = job_tiles(jw);
+                        q2 = job_q(jw);
                         idx = (uint32_t)old;
-                        ok = g2 == (uint32_t)(old >> 32) && k2 != kJobNone && idx < t2;
+                        ok = job_gen(jw) == (uint32_t)(old >> 32) && k2 != kJobNone && idx < t2;
                     }
                     ok = __shfl_sync(kFull, ok, l);
                     if (ok) {
                         found = __shfl_sync(kFull, si, l);
                         f_kind = __shfl_sync(kFull, k2, l);
                         f_tiles = __shfl_sync(kFull, t2, l);
+                        f_q = __shfl_sync(kFull, q2, l);
                         f_tile = __shfl_sync(kFull, idx, l);
                         break;
                     }
@@ -490,6 +502,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
                 if (found >= 0) {
                     s_kind = f_kind;
                     s_tiles = f_tiles;
+                    s_q = f_q;
                     s_tile = (long long)f_tile;
                 }
             }
@@ -533,8 +546,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
         const uint32_t kind = s_kind;
         if (kind == kJobInit) init_tile(P, S, s_tile);
         else if (kind == kJobCheck) check_tile(P, S, s_tile);
-        else if (((const volatile Slot *)S)->kind == 1) relax_tile<true>(P, S, s_tile, s_wb[warp], s_ws[warp]);
-        else relax_tile<false>(P, S, s_tile, s_wb[warp], s_ws[warp]);
+        else if (((const volatile Slot *)S)->kind == 1) relax_tile<true>(P, S, s_tile, s_q, s_wb[warp], s_ws[warp]);
+        else relax_tile<false>(P, S, s_tile, s_q, s_wb[warp], s_ws[warp]);
         // Other CTAs read this tile's stores (list entries, resets) in the
         // slot's next job within this same kernel: every thread makes its own
         // stores visible device-wide before the tile is counted as done.
@@ -847,6 +860,64 @@ lb_status lb_server_poll(lb_server *s, lb_completion *out, int32_t cap, int32_t 
     }
     *ndone = k;
     lb_status st = ensure_running(s);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    return st;
+}
+
+lb_status lb_server_state(lb_server *s, lb_server_state_t *out) {
+    if (!s || !out) return sfail(LB_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof(*out));
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    // read through a side stream: the persistent kernel may be running
+    cudaStream_t side = nullptr;
+    lb_status st = LB_OK;
+    Shared sh;
+    std::vector<Slot> slots((size_t)s->nslots);
+    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sh, s->d_shared, sizeof(Shared), cudaMemcpyDeviceToHost, side);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(slots.data(), s->d_slots, sizeof(Slot) * slots.size(), cudaMemcpyDeviceToHost, side);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(side);
+    if (side) cudaStreamDestroy(side);
+    if (e != cudaSuccess) {
+        st = sfail(LB_ERR_CUDA, "reading server state", e);
+    } else {
+        out->submitted = (int64_t)s->submitted;
+        out->consumed = (int64_t)sh.consumed;
+        out->completed = (int64_t)sh.completed;
+        out->acked = (int64_t)s->acked;
+        out->active = (int32_t)sh.active;
+        out->stopping = (int32_t)sh.stopping;
+        out->admit_lock = (int32_t)sh.admit_lock;
+        out->kernel_error = (int32_t)sh.error;
+        out->kernel_running = kernel_running(s) ? 1 : 0;
+        int32_t k = 0;
+        for (size_t i = 0; i < slots.size(); ++i) {
+            const Slot &S = slots[i];
+            if (!S.busy) continue;
+            out->busy_slots++;
+            if (k < 16) {
+                lb_slot_state_t &d = out->slot[k++];
+                d.slot = (int32_t)i;
+                d.graph = S.graph;
+                d.kind = S.kind;
+                d.level = (int32_t)S.level;
+                d.job_kind = (int32_t)job_kind(S.job);
+                d.job_tiles = (int32_t)job_tiles(S.job);
+                d.job_done = (int32_t)S.job_done;
+                d.job_gen = (int32_t)job_gen(S.job);
+                d.claim = (int64_t)S.claim;
+                d.in_cnt = (int64_t)S.in_cnt;
+                d.in_edges = (int64_t)S.in_edges;
+                d.error = (int32_t)S.error;
+                d.ticket = (int64_t)S.ticket;
+            }
+        }
+        out->listed = k;
+    }
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     return st;
 }

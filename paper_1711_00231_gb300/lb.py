@@ -78,6 +78,22 @@ class lb_completion(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("edges_relaxed", ctypes.c_int64), ("device_ns", ctypes.c_int64)]
 
 
+class lb_slot_state_t(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_int32), ("graph", ctypes.c_int32), ("kind", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("job_kind", ctypes.c_int32), ("job_tiles", ctypes.c_int32), ("job_done", ctypes.c_int32),
+                ("job_gen", ctypes.c_int32), ("claim", ctypes.c_int64), ("in_cnt", ctypes.c_int64),
+                ("in_edges", ctypes.c_int64), ("error", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ticket", ctypes.c_int64)]
+
+
+class lb_server_state_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("consumed", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("acked", ctypes.c_int64), ("active", ctypes.c_int32), ("stopping", ctypes.c_int32),
+                ("admit_lock", ctypes.c_int32), ("kernel_error", ctypes.c_int32), ("kernel_running", ctypes.c_int32),
+                ("busy_slots", ctypes.c_int32), ("listed", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("slot", lb_slot_state_t * 16)]
+
+
 class lb_step_record(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("mode", ctypes.c_int32), ("list_size", ctypes.c_int64),
                 ("edges", ctypes.c_int64), ("t_ns", ctypes.c_int64)]
@@ -121,6 +137,7 @@ def _load():
         "lb_server_submit": ([P, i32, i32, i32, P, ctypes.POINTER(ctypes.c_uint64)], st),
         "lb_server_poll": ([P, P, i32, ctypes.POINTER(i32)], st),
         "lb_server_stop": ([P], st),
+        "lb_server_state": ([P, ctypes.POINTER(lb_server_state_t)], st),
         "lb_last_error": ([], ctypes.c_char_p),
         "lb_version": ([], ctypes.c_char_p),
     }
@@ -362,6 +379,16 @@ def lb_server_poll(s: int, cap: int = _POLL_CAP):
     _check(_load().lb_server_poll(s, ctypes.cast(_poll_buf, ctypes.c_void_p), cap, ctypes.byref(n)))
     return [(int(c.ticket), int(c.status), int(c.graph), int(c.iterations), int(c.edges_relaxed), int(c.device_ns))
             for c in _poll_buf[:n.value]]
+
+
+def lb_server_state(s: int) -> dict:
+    """Diagnostic snapshot of the serving engine (counters and busy slots)."""
+    x = lb_server_state_t()
+    _check(_load().lb_server_state(s, ctypes.byref(x)))
+    d = {k: int(getattr(x, k)) for k, _ in x._fields_ if k not in ("slot", "pad")}
+    d["slots"] = [{k: int(getattr(x.slot[i], k)) for k, _ in lb_slot_state_t._fields_ if k != "pad"}
+                  for i in range(x.listed)]
+    return d
 
 
 def lb_server_stop(s: int) -> None:

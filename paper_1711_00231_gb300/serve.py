@@ -51,6 +51,9 @@ class Server:
     def stop(self):
         lb.lb_server_stop(self.h)
 
+    def state(self) -> dict:
+        return lb.lb_server_state(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             lb.lb_server_destroy(self.h)
@@ -75,7 +78,7 @@ class Server:
                 status[tick[c[0]]] = c[1]
                 left -= 1
             if left and time.perf_counter() > t_end:
-                raise TimeoutError(f"{left} queries still running")
+                raise TimeoutError(f"{left} queries still running; engine state {self.state()}")
         return status
 
 
@@ -112,7 +115,7 @@ def serve(server: Server, reqs: Sequence[Request], outs, timeout_s: float = 600.
                 status[i] = c[1]
                 left -= 1
         if now > timeout_s:
-            raise TimeoutError(f"{left} queries unfinished")
+            raise TimeoutError(f"{left} queries unfinished; engine state {server.state()}")
     span = done_at.max() - min(r.arrival_s for r in reqs)
     res = {"queries": len(reqs), "seconds": float(span), "qps": len(reqs) / span,
            "statuses_ok": all(s == 0 for s in status)}

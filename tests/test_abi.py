@@ -47,17 +47,20 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lb_options), sizeof(lb_mem_stats), sizeof(lb_query_stats), sizeof(lb_step_record));
   printf("%zu %zu %zu %zu\n", offsetof(lb_query_stats, status), offsetof(lb_query_stats, device_ms), offsetof(lb_mem_stats, ns_split), offsetof(lb_step_record, t_ns));
+  printf("%zu %zu %zu %zu\n", sizeof(lb_server_state_t), sizeof(lb_slot_state_t), offsetof(lb_server_state_t, slot), offsetof(lb_slot_state_t, ticket));
   return 0;
 }''')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
-    a, b = subprocess.check_output([str(exe)], text=True).strip().splitlines()
+    a, b, c = subprocess.check_output([str(exe)], text=True).strip().splitlines()
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(lb.lb_options), ctypes.sizeof(lb.lb_mem_stats), ctypes.sizeof(lb.lb_query_stats),
                      ctypes.sizeof(lb.lb_step_record)]
     assert offs == [lb.lb_query_stats.status.offset, lb.lb_query_stats.device_ms.offset, lb.lb_mem_stats.ns_split.offset,
                     lb.lb_step_record.t_ns.offset]
+    assert [int(x) for x in c.split()] == [ctypes.sizeof(lb.lb_server_state_t), ctypes.sizeof(lb.lb_slot_state_t),
+                                           lb.lb_server_state_t.slot.offset, lb.lb_slot_state_t.ticket.offset]
 
 
 def test_version_and_error_string():

@@ -138,6 +138,28 @@ def test_many_small_rounds_with_few_slots(mix):
         S.close()
 
 
+def test_many_jobs_in_flight(mix):
+    # many slots busy at once with small tiles: jobs open and close on every
+    # slot while hundreds of CTAs scan and claim, so a claim taken against a
+    # job that has just been replaced is common; every result must be exact
+    import torch
+    graphs, handles = mix
+    S = sv.Server(handles, slots=96, tile=256)
+    try:
+        for rep in range(2):
+            reqs = make_requests(graphs, 400, seed=31 + rep)
+            outs = [torch.empty(graphs[r.graph].n, dtype=torch.int32, device="cuda") for r in reqs]
+            st = S.run_batch(reqs, outs, timeout_s=120)
+            assert all(x == 0 for x in st), st
+            torch.cuda.synchronize()
+            for r, o in zip(reqs, outs):
+                assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src)), r
+        state = S.state()
+        assert state["busy_slots"] == 0 and state["active"] == 0 and state["completed"] == 800
+    finally:
+        S.close()
+
+
 def test_overflow_and_invalid_requests(mix):
     import torch
     graphs, handles = mix
