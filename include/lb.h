@@ -311,6 +311,7 @@ typedef struct lb_server_state_t {
     int64_t submitted, consumed, completed, acked;
     int32_t active, stopping, admit_lock, kernel_error;
     int32_t kernel_running, busy_slots, listed, pad;
+    int64_t prof[8];    /* per-phase cycle counters of a profiling build, else 0 */
     lb_slot_state_t slot[16];
 } lb_server_state_t;
 

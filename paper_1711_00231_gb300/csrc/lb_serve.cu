@@ -38,6 +38,25 @@ namespace srv {
 constexpr uint32_t kRing = 1u << 16;         // request / completion ring entries
 constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
 constexpr int kItems = 2;
+constexpr uint64_t kAdmitPeriodNs = 50000;  // a busy CTA retries admission this often
+
+// Slot scheduling: 1 = round robin (after a tile a CTA moves on to the next
+// slot, except that the CTA that opened a slot's next job takes its first
+// tile) plus admission by busy CTAs; 0 = a CTA keeps to the slot it last
+// claimed from, and only CTAs without work admit requests.
+#ifndef LB_SERVE_POLICY
+#define LB_SERVE_POLICY 1
+#endif
+
+// Build with -DLB_SERVE_PROFILE=1 to count SM cycles per phase of the
+// persistent loop (thread 0 of every CTA; summed when a CTA leaves):
+// 0 scan + claim that found a tile, 1 loops without a tile (scan,
+// admission, back-off), 2 tile body up to the block barrier, 3 done count
+// and job finalisation, 4 admission by busy CTAs, 5 tiles, 6 jobs finished,
+// 7 loops without a tile.
+#ifndef LB_SERVE_PROFILE
+#define LB_SERVE_PROFILE 0
+#endif
 
 enum : uint32_t { kJobNone = 0, kJobInit = 1, kJobRelax = 2, kJobCheck = 3 };
 
@@ -122,6 +141,7 @@ struct Shared {  // device-global control of the persistent kernel
     unsigned long long consumed;
     unsigned long long completed;
     unsigned long long kernel_t0;
+    unsigned long long prof[8];  // per-phase cycle counters (LB_SERVE_PROFILE)
 };
 
 struct Params {
@@ -257,8 +277,9 @@ __device__ int32_t slot_status(const Slot *S) {
     return LB_OK;
 }
 
-// Finalises the slot's job after its last tile (single thread).
-__device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
+// Finalises the slot's job after its last tile (single thread).  Returns
+// true when the slot has a next job open.
+__device__ bool finish_job(const Params &P, Slot *S, uint32_t kind) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
     const int64_t T = P.tile;
@@ -272,7 +293,7 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
         if (deg == 0) {
             S->level = 1;
             complete_query(P, S, LB_OK);
-            return;
+            return false;
         }
         NodeList L = S->lists[0];
         L.v[0] = st.src;
@@ -285,7 +306,7 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
         S->in_edges = (uint64_t)deg;
         const int64_t Tj = iteration_tile(deg, gridDim.x, T);
         open_job(S, kJobRelax, (uint32_t)((deg + Tj - 1) / Tj), (uint32_t)(Tj / kTileGrain));
-        return;
+        return true;
     }
     if (kind == kJobRelax) {
         const unsigned long long pk = ld_volatile(&S->out_pack);
@@ -304,17 +325,18 @@ __device__ void finish_job(const Params &P, Slot *S, uint32_t kind) {
             S->out_pack = 0ull;
             const int64_t Tj = iteration_tile(edges, gridDim.x, T);
             open_job(S, kJobRelax, (uint32_t)((edges + Tj - 1) / Tj), (uint32_t)(Tj / kTileGrain));
-            return;
+            return true;
         }
         if (cnt > 0 && !(err & (kErrCapacity | kErrBounds))) atomicOr(&S->error, kErrIterCap);
         if (st.kind == 1 && (err & kErrSaturated)) {
             open_job(S, kJobCheck, (uint32_t)((g.n + kInitChunk - 1) / kInitChunk));
-            return;
+            return true;
         }
         complete_query(P, S, slot_status(S));
-        return;
+        return false;
     }
     complete_query(P, S, slot_status(S));  // kJobCheck
+    return false;
 }
 
 // ---- tile bodies (block-wide) ------------------------------------------------
@@ -429,6 +451,25 @@ __device__ void admit(const Params &P) {
     st_release_sys(&P.host->consumed, con);
 }
 
+// Takes the admission lock if free and, unless the grid is leaving, admits
+// pending requests into free slots (thread 0 of a CTA).  Returns whether
+// the lock was taken; *admitted tells whether any request was admitted.
+__device__ bool try_admit(const Params &P, bool *admitted) {
+    *admitted = false;
+    if (atomicCAS(&P.sh->admit_lock, 0u, 1u) != 0u) return false;
+    if (__ldcg(&P.sh->stopping) == 0u) {
+        const unsigned long long before = __ldcg(&P.sh->consumed);
+        admit(P);
+        *admitted = __ldcg(&P.sh->consumed) != before;
+    }
+    return true;
+}
+
+__device__ void release_admit(const Params &P) {
+    __threadfence();
+    atomicExch(&P.sh->admit_lock, 0u);
+}
+
 // ---- the persistent kernel -------------------------------------------------
 
 __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
@@ -438,19 +479,32 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
     __shared__ uint32_t s_kind, s_tiles, s_q;
     __shared__ long long s_tile;
     __shared__ int s_exit;
+    __shared__ uint32_t s_scan_from;
     const uint32_t warp = threadIdx.x >> 5;
     uint64_t idle_since = 0;
-    uint32_t scan_from = blockIdx.x % (uint32_t)P.nslots;
+    uint64_t last_admit = 0;
+#if LB_SERVE_PROFILE
+    unsigned long long pf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long c_top = 0, c_mid = 0;
+#define PF_MARK(v) (v) = clock64()
+#define PF_ADD(i, v) pf[i] += (unsigned long long)((v))
+#else
+#define PF_MARK(v)
+#define PF_ADD(i, v)
+#endif
+    if (threadIdx.x == 0) s_scan_from = blockIdx.x % (uint32_t)P.nslots;
     for (;;) {
         // every thread has read the previous iteration's s_* values before
         // thread 0 overwrites them (without this barrier a lagging warp could
         // pick up the next tile out of step with its block)
         __syncthreads();
+        if (threadIdx.x == 0) PF_MARK(c_top);
         if (threadIdx.x < 32) {
             // warp 0 looks at 32 slots per round: each lane reads one slot's
             // claim word and job fields, and the claimable slots are tried in
             // order until a claim holds (one L2 round trip per 32 slots)
             const uint32_t lane = threadIdx.x;
+            const uint32_t scan_from = s_scan_from;
             int found = -1;
             uint32_t f_kind = 0, f_tiles = 0, f_tile = 0, f_q = 0;
             for (int32_t c0 = 0; c0 < P.nslots && found < 0; c0 += 32) {
@@ -495,8 +549,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
                     }
                 }
             }
-            if (found >= 0) scan_from = (uint32_t)found;  // every lane keeps the same start
             if (lane == 0) {
+                if (found >= 0) s_scan_from = (uint32_t)found;
                 s_slot = found;
                 s_exit = 0;
                 if (found >= 0) {
@@ -512,11 +566,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
                 const uint64_t now = global_ns();
                 // Admission and the decision to stop are taken under one lock,
                 // so no request is admitted after the grid decided to leave.
-                if (atomicCAS(&P.sh->admit_lock, 0u, 1u) == 0u) {
+                bool admitted = false;
+                if (try_admit(P, &admitted)) {
+                    last_admit = now;
                     if (__ldcg(&P.sh->stopping) == 0u) {
-                        const unsigned long long before = __ldcg(&P.sh->consumed);
-                        admit(P);
-                        const bool admitted = __ldcg(&P.sh->consumed) != before;
                         if (admitted || __ldcg(&P.sh->active) != 0u) {
                             idle_since = 0;
                         } else if (idle_since == 0) {
@@ -525,8 +578,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
                             atomicExch(&P.sh->stopping, 1u);
                         }
                     }
-                    __threadfence();
-                    atomicExch(&P.sh->admit_lock, 0u);
+                    release_admit(P);
                 }
                 if (ld_acquire_sys32(&P.host->stop) != 0u || __ldcg(&P.sh->stopping) != 0u) s_exit = 1;
                 if (now - __ldcg(&P.sh->kernel_t0) > P.hard_ns) {
@@ -539,7 +591,20 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
             }
         }
         __syncthreads();
+#if LB_SERVE_PROFILE
+        if (threadIdx.x == 0) {
+            PF_MARK(c_mid);
+            if (s_slot >= 0) PF_ADD(0, c_mid - c_top);
+            else { PF_ADD(1, c_mid - c_top); PF_ADD(7, 1); }
+        }
+        if (s_exit) {
+            if (threadIdx.x == 0)
+                for (int i = 0; i < 8; ++i) atomicAdd(&P.sh->prof[i], pf[i]);
+            break;
+        }
+#else
         if (s_exit) break;
+#endif
         const int si = s_slot;
         if (si < 0) continue;
         Slot *S = &P.slots[si];
@@ -554,12 +619,43 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
+#if LB_SERVE_PROFILE
+            long long c_b = clock64();
+            PF_ADD(2, c_b - c_mid);
+            PF_ADD(5, 1);
+#endif
             __threadfence();
             const uint32_t d = atomicAdd(&S->job_done, 1u);
+            bool reopened = false;
             if (d == s_tiles - 1) {
                 __threadfence();
-                finish_job(P, S, kind);
+                reopened = finish_job(P, S, kind);
+                PF_ADD(6, 1);
             }
+#if LB_SERVE_PROFILE
+            long long c_d = clock64();
+            PF_ADD(3, c_d - c_b);
+#endif
+#if LB_SERVE_POLICY == 1
+            // round robin, except that the CTA which opened the slot's next
+            // job takes its first tile (a query's chain of small iterations
+            // then runs without waiting for a scan to come by)
+            s_scan_from = reopened ? (uint32_t)si : ((uint32_t)si + 1u) % (uint32_t)P.nslots;
+            // busy CTAs also refill free slots, so that admission does not
+            // wait until some CTA runs out of work
+            const uint64_t now = global_ns();
+            if (now - last_admit > kAdmitPeriodNs && __ldcg(&P.sh->active) < (uint32_t)P.nslots) {
+                last_admit = now;
+                bool admitted = false;
+                if (try_admit(P, &admitted)) release_admit(P);
+            }
+#if LB_SERVE_PROFILE
+            PF_ADD(4, clock64() - c_d);
+#endif
+#else
+            (void)reopened;
+            (void)last_admit;
+#endif
         }
     }
 }
@@ -894,6 +990,7 @@ lb_status lb_server_state(lb_server *s, lb_server_state_t *out) {
         out->admit_lock = (int32_t)sh.admit_lock;
         out->kernel_error = (int32_t)sh.error;
         out->kernel_running = kernel_running(s) ? 1 : 0;
+        for (int i = 0; i < 8; ++i) out->prof[i] = (int64_t)sh.prof[i];
         int32_t k = 0;
         for (size_t i = 0; i < slots.size(); ++i) {
             const Slot &S = slots[i];

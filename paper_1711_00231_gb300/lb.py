@@ -91,7 +91,7 @@ class lb_server_state_t(ctypes.Structure):
                 ("acked", ctypes.c_int64), ("active", ctypes.c_int32), ("stopping", ctypes.c_int32),
                 ("admit_lock", ctypes.c_int32), ("kernel_error", ctypes.c_int32), ("kernel_running", ctypes.c_int32),
                 ("busy_slots", ctypes.c_int32), ("listed", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("slot", lb_slot_state_t * 16)]
+                ("prof", ctypes.c_int64 * 8), ("slot", lb_slot_state_t * 16)]
 
 
 class lb_step_record(ctypes.Structure):
@@ -385,7 +385,8 @@ def lb_server_state(s: int) -> dict:
     """Diagnostic snapshot of the serving engine (counters and busy slots)."""
     x = lb_server_state_t()
     _check(_load().lb_server_state(s, ctypes.byref(x)))
-    d = {k: int(getattr(x, k)) for k, _ in x._fields_ if k not in ("slot", "pad")}
+    d = {k: int(getattr(x, k)) for k, _ in x._fields_ if k not in ("slot", "pad", "prof")}
+    d["prof"] = [int(v) for v in x.prof]
     d["slots"] = [{k: int(getattr(x.slot[i], k)) for k, _ in lb_slot_state_t._fields_ if k != "pad"}
                   for i in range(x.listed)]
     return d
