@@ -252,7 +252,9 @@ typedef struct lb_server_options {
     int32_t slots;        /* queries in flight at most; 0 = as many as fit in
                              mem_fraction of free HBM, at most 256 */
     int32_t ctas_per_sm;  /* persistent grid: CTAs per SM (0 = occupancy) */
-    int32_t tile;         /* worklist edges per work tile (0 = 2048) */
+    int32_t tile;         /* largest work tile in worklist edges, 256..8192
+                             (0 = 8192); a job's tiles shrink to spread it
+                             over its share of the grid */
     int32_t idle_us;      /* the kernel exits after this long with no work
                              (0 = 1000); it is relaunched on demand */
     double mem_fraction;  /* share of free HBM the slots may take (0 = 0.5) */

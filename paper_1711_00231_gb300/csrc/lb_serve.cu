@@ -58,6 +58,15 @@ constexpr uint64_t kAdmitPeriodNs = 50000;  // a busy CTA retries admission this
 #define LB_SERVE_PROFILE 0
 #endif
 
+// Completion of a tile: 0 = block barrier, then one device-scope fence by
+// thread 0 before the done count (the pattern of a cooperative grid
+// barrier: the barrier orders the block's stores before thread 0's fence);
+// 1 = every thread fences its own stores before the barrier as well.
+#ifndef LB_SERVE_TILE_FENCE
+#define LB_SERVE_TILE_FENCE 0
+#endif
+
+
 enum : uint32_t { kJobNone = 0, kJobInit = 1, kJobRelax = 2, kJobCheck = 3 };
 
 struct Req {
@@ -159,6 +168,16 @@ struct Params {
     uint64_t idle_ns;
     uint64_t hard_ns;
 };
+
+// Tile size of a RELAX job: the job's share of the grid is the grid divided
+// by the busy slots, so with many queries in flight each job gets fewer,
+// longer tiles (less claiming and finalising per edge), and a query alone
+// spreads over the whole grid.
+__device__ __forceinline__ int64_t job_tile(const Params &P, int64_t edges) {
+    const uint32_t busy = __ldcg(&P.sh->active);
+    const int64_t share = busy > 1 ? max((int64_t)1, (int64_t)gridDim.x / (int64_t)busy) : (int64_t)gridDim.x;
+    return iteration_tile(edges, share, P.tile);
+}
 
 // ---- coherent (L2) loads and system-scope accesses ------------------------
 
@@ -282,7 +301,6 @@ __device__ int32_t slot_status(const Slot *S) {
 __device__ bool finish_job(const Params &P, Slot *S, uint32_t kind) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
-    const int64_t T = P.tile;
     if (kind == kJobInit) {
         const int64_t beg = g.off[st.src];
         const int64_t deg = g.off[st.src + 1] - beg;
@@ -304,7 +322,7 @@ __device__ bool finish_job(const Params &P, Slot *S, uint32_t kind) {
         for (int64_t k = 0; k < grains && k < P.tile_cap; ++k) L.tstart[k] = 0;
         S->in_cnt = 1;
         S->in_edges = (uint64_t)deg;
-        const int64_t Tj = iteration_tile(deg, gridDim.x, T);
+        const int64_t Tj = job_tile(P, deg);
         open_job(S, kJobRelax, (uint32_t)((deg + Tj - 1) / Tj), (uint32_t)(Tj / kTileGrain));
         return true;
     }
@@ -323,7 +341,7 @@ __device__ bool finish_job(const Params &P, Slot *S, uint32_t kind) {
             S->in_cnt = (uint32_t)cnt;
             S->in_edges = (uint64_t)edges;
             S->out_pack = 0ull;
-            const int64_t Tj = iteration_tile(edges, gridDim.x, T);
+            const int64_t Tj = job_tile(P, edges);
             open_job(S, kJobRelax, (uint32_t)((edges + Tj - 1) / Tj), (uint32_t)(Tj / kTileGrain));
             return true;
         }
@@ -614,9 +632,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
         else if (((const volatile Slot *)S)->kind == 1) relax_tile<true>(P, S, s_tile, s_q, s_wb[warp], s_ws[warp]);
         else relax_tile<false>(P, S, s_tile, s_q, s_wb[warp], s_ws[warp]);
         // Other CTAs read this tile's stores (list entries, resets) in the
-        // slot's next job within this same kernel: every thread makes its own
-        // stores visible device-wide before the tile is counted as done.
+        // slot's next job within this same kernel: they are made visible
+        // device-wide before the tile is counted as done.
+#if LB_SERVE_TILE_FENCE
         __threadfence();
+#endif
         __syncthreads();
         if (threadIdx.x == 0) {
 #if LB_SERVE_PROFILE
@@ -799,7 +819,7 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     lb_server_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.tile == 0) o.tile = 2048;
+    if (o.tile == 0) o.tile = 8192;
     if (o.idle_us == 0) o.idle_us = 1000;
     if (o.mem_fraction <= 0.0) o.mem_fraction = 0.5;
     if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > 4096 || o.idle_us < 0 ||

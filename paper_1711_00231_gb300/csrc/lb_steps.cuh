@@ -11,6 +11,15 @@
 #ifndef LB_WD_MIN_BLOCKS
 #define LB_WD_MIN_BLOCKS 6
 #endif
+#ifndef LB_WD_MIN_BLOCKS_SSSP
+#define LB_WD_MIN_BLOCKS_SSSP LB_WD_MIN_BLOCKS
+#endif
+// Whether the SSSP walk keeps its look-ahead window across steps and skips
+// the boundary search inside one adjacency list, as the BFS walk does (it
+// needs more registers in the SSSP kernel, which also loads the source id).
+#ifndef LB_WD_FAST_SSSP
+#define LB_WD_FAST_SSSP 0
+#endif
 
 
 namespace lbk {
@@ -244,6 +253,12 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
     int32_t scur = ld_list<COH>(in.scan + kcur);
     int32_t bcur = ld_list<COH>(in.beg + kcur);
     int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
+    // look-ahead window: lane l holds entry kcur + 1 + l; it stays valid
+    // until the walk advances, so steps inside one long adjacency list
+    // (most edges of a skewed graph) load no list entries at all
+    constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
+    int32_t sj = INT32_MAX, bj = 0, uj = 0;
+    bool fresh = false;
     for (int64_t ew = w0; ew < w1; ew += 32 * STEPS) {
         int32_t vv[STEPS];
         uint32_t ww[STEPS], dd[STEPS];
@@ -257,31 +272,44 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
             ww[st] = 0;
             dd[st] = 0;
             if (es >= w1) continue;  // warp-uniform
-            const int64_t j = kcur + 1 + lane;
-            int32_t sj = INT32_MAX, bj = 0;
-            int32_t uj = 0;
-            if (j < ihi) {
-                sj = ld_list<COH>(in.scan + j);
-                bj = ld_list<COH>(in.beg + j);
-                if (SSSP) uj = ld_list<COH>(in.v + j);
+            if (!kFast || !fresh) {
+                const int64_t j = kcur + 1 + lane;
+                sj = INT32_MAX;
+                bj = 0;
+                uj = 0;
+                if (j < ihi) {
+                    sj = ld_list<COH>(in.scan + j);
+                    bj = ld_list<COH>(in.beg + j);
+                    if (SSSP) uj = ld_list<COH>(in.v + j);
+                }
+                fresh = true;
             }
-            const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
-            const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
-            const int c = __popc(starts & upto);
-            const int src_lane = c > 0 ? c - 1 : 0;
-            const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
-            const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
-            const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
-            const int32_t s_l = c > 0 ? s_sh : scur;
-            const int32_t b_l = c > 0 ? b_sh : bcur;
-            const int32_t u_l = c > 0 ? u_sh : ucur;  // taken before the walk advances
-            // advance to the entry holding the next step's first edge
-            const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
-            if (adv > 0) {
-                scur = __shfl_sync(kFull, sj, adv - 1);
-                bcur = __shfl_sync(kFull, bj, adv - 1);
-                if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
-                kcur += adv;
+            int32_t s_l = scur, b_l = bcur, u_l = ucur;
+            // first edge of entry kcur + 1: if it lies beyond this step and the
+            // next step's first edge, every lane stays in entry kcur
+            if (!kFast || (int64_t)__shfl_sync(kFull, sj, 0) <= es + 32) {  // warp-uniform
+                const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
+                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
+                const int c = __popc(starts & upto);
+                const int src_lane = c > 0 ? c - 1 : 0;
+                const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
+                const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
+                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
+                if (c > 0) {
+                    s_l = s_sh;
+                    b_l = b_sh;
+                    u_l = u_sh;  // taken before the walk advances
+                }
+                // advance to the entry holding the next step's first edge
+                // (at least one entry on the fast path)
+                const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
+                if (adv > 0) {
+                    scur = __shfl_sync(kFull, sj, adv - 1);
+                    bcur = __shfl_sync(kFull, bj, adv - 1);
+                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
+                    kcur += adv;
+                    fresh = false;
+                }
             }
             if (e < w1) {
                 const int64_t eidx = (int64_t)b_l + (e - (int64_t)s_l);
@@ -314,7 +342,7 @@ __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const Nod
 }
 
 template <bool SSSP, int ITEMS>
-__global__ void __launch_bounds__(kBlock, LB_WD_MIN_BLOCKS) k_step_wd(StepParams p) {
+__global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_MIN_BLOCKS) k_step_wd(StepParams p) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
     Ctl *ctl = p.ctl;
