@@ -87,8 +87,8 @@ typedef struct lb_options {
                               conditional WHILE node); 1: host loop with a
                               worklist-size readback per iteration, as in the
                               paper's drivers (0) */
-    int32_t wd_tile;       /* largest WD tile in worklist edges: 256..8192,
-                              a multiple of 256 (2048); each iteration uses
+    int32_t wd_tile;       /* largest WD tile in worklist edges: 256..32768,
+                              a multiple of 256 (8192); each iteration uses
                               the smallest multiple of 256 up to this that
                               gives every CTA about two tiles */
     int32_t ctas_per_sm;   /* CTAs per SM the fixed relax grid is sized for;

@@ -173,7 +173,7 @@ lb_options default_options() {
     o.mdt_override = 0;
     o.hp_threshold = 1024;
     o.loop_mode = 0;
-    o.wd_tile = 2048;
+    o.wd_tile = 8192;
     o.ctas_per_sm = 0;
     return o;
 }
@@ -187,7 +187,7 @@ lb_status normalise_options(const lb_options *in, lb_options *out) {
     if (o.hist_bins < 1 || o.hist_bins > 4096) return fail(LB_ERR_ARG, "hist_bins must be in [1, 4096]");
     if (o.mdt_override < 0) return fail(LB_ERR_ARG, "mdt_override must be >= 0");
     if (o.loop_mode != 0 && o.loop_mode != 1) return fail(LB_ERR_ARG, "loop_mode must be 0 or 1");
-    if (o.wd_tile < 256 || o.wd_tile > 8192 || o.wd_tile % 256) return fail(LB_ERR_ARG, "wd_tile must be a multiple of 256 in [256, 8192]");
+    if (o.wd_tile < 256 || o.wd_tile > 32768 || o.wd_tile % 256) return fail(LB_ERR_ARG, "wd_tile must be a multiple of 256 in [256, 32768]");
     if (o.ctas_per_sm < 0 || o.ctas_per_sm > 32) return fail(LB_ERR_ARG, "ctas_per_sm must be in [0, 32]");
     *out = o;
     return LB_OK;
@@ -821,7 +821,7 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
     const lb_options base = g->opt;
     // candidate grid: tile sizes and grid shapes for every strategy, plus the
     // HP list-size threshold where it matters
-    const int32_t tiles[] = {512, 1024, 2048, 4096};
+    const int32_t tiles[] = {1024, 2048, 4096, 8192, 16384};
     const int32_t ctas[] = {0, 2, 3};
     const int32_t thr[] = {256, 1024, 4096};
     std::vector<lb_options> cands;
@@ -835,7 +835,7 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
                     o.hp_threshold = h;
                     cands.push_back(o);
                 }
-            } else if (s == LB_WD || is_ep(s) || c == 0 || t == 2048) {
+            } else if (s == LB_WD || is_ep(s) || c == 0 || t == 8192) {
                 lb_options o = base;
                 o.wd_tile = t;
                 o.ctas_per_sm = c;

@@ -95,9 +95,19 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, ui
     return lo;
 }
 
-// Warp-uniform flush of a warp push buffer into a global list.
+// Warp-uniform flush of a warp push buffer into a global list.  It runs
+// once per ~100 pushes; LB_FLUSH_NOINLINE=1 keeps it out of line so its
+// registers do not count against the relax loops around it.
+#ifndef LB_FLUSH_NOINLINE
+#define LB_FLUSH_NOINLINE 0
+#endif
+#if LB_FLUSH_NOINLINE
+#define LB_FLUSH_INLINE __noinline__
+#else
+#define LB_FLUSH_INLINE inline
+#endif
 template <int KIND, bool TILED>
-__device__ inline void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
+__device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
     if (cnt == 0) return;
     const uint32_t lane = lane_id();
     uint32_t run_u = 0, run_e = 0;

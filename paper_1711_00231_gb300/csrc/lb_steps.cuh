@@ -18,7 +18,11 @@
 // the boundary search inside one adjacency list, as the BFS walk does (it
 // needs more registers in the SSSP kernel, which also loads the source id).
 #ifndef LB_WD_FAST_SSSP
-#define LB_WD_FAST_SSSP 0
+#define LB_WD_FAST_SSSP 1
+#endif
+// Edges a lane loads ahead in the run loop (more loads in flight per warp).
+#ifndef LB_WD_RUN_ITEMS
+#define LB_WD_RUN_ITEMS 2
 #endif
 
 
@@ -259,7 +263,61 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
     constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
     int32_t sj = INT32_MAX, bj = 0, uj = 0;
     bool fresh = false;
-    for (int64_t ew = w0; ew < w1; ew += 32 * STEPS) {
+    int64_t ew = w0;
+    while (ew < w1) {  // warp-uniform
+        if (!kFast || !fresh) {
+            const int64_t j = kcur + 1 + lane;
+            sj = INT32_MAX;
+            bj = 0;
+            uj = 0;
+            if (j < ihi) {
+                sj = ld_list<COH>(in.scan + j);
+                bj = ld_list<COH>(in.beg + j);
+                if (SSSP) uj = ld_list<COH>(in.v + j);
+            }
+            fresh = true;
+        }
+        if (kFast) {
+            // first edge of entry kcur + 1: when no entry starts inside the
+            // next 32 edges, run through entry kcur's edges up to that start
+            // with a plain strided loop (no boundary search per step)
+            const int64_t s_next = (int64_t)__shfl_sync(kFull, sj, 0);
+            if (s_next > ew + 32) {
+                const int64_t rend = min(s_next, w1);
+                const int64_t base = (int64_t)bcur - (int64_t)scur;  // edge id = base + list edge
+                if (base + ew < 0 || base + rend > g.m) {
+                    if (lane == 0) atomicOr(err, kErrBounds);
+                    return;
+                }
+                uint32_t du = 0;
+                if (SSSP) du = ld_mut<COH>(epoch + ucur) == stamp ? kInf : ld_mut<COH>(status + ucur);
+                constexpr int R = LB_WD_RUN_ITEMS;
+                for (int64_t x = ew; x < rend; x += 32 * R) {
+                    int32_t vv[R];
+                    uint32_t ww[R], dd[R];
+                    bool ok[R];
+#pragma unroll
+                    for (int st = 0; st < R; ++st) {
+                        const int64_t e = x + 32 * st + lane;
+                        ok[st] = e < rend;
+                        vv[st] = ok[st] ? __ldg(g.col + (base + e)) : 0;
+                        ww[st] = (SSSP && ok[st]) ? __ldg(g.w + (base + e)) : 0u;
+                        dd[st] = du;
+                    }
+                    relax_items<SSSP, R, kOutNode, true, COH>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level,
+                                                              stamp, err, wb, ws, cnt, o);
+                }
+                ew = rend;
+                if (rend == s_next) {  // entry kcur + 1 starts at ew
+                    scur = (int32_t)s_next;
+                    bcur = __shfl_sync(kFull, bj, 0);
+                    if (SSSP) ucur = __shfl_sync(kFull, uj, 0);
+                    kcur += 1;
+                    fresh = false;
+                }
+                continue;
+            }
+        }
         int32_t vv[STEPS];
         uint32_t ww[STEPS], dd[STEPS];
         bool ok[STEPS];
@@ -272,7 +330,7 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
             ww[st] = 0;
             dd[st] = 0;
             if (es >= w1) continue;  // warp-uniform
-            if (!kFast || !fresh) {
+            if (st > 0 && !fresh) {  // the previous step advanced: reload the window
                 const int64_t j = kcur + 1 + lane;
                 sj = INT32_MAX;
                 bj = 0;
@@ -285,31 +343,26 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
                 fresh = true;
             }
             int32_t s_l = scur, b_l = bcur, u_l = ucur;
-            // first edge of entry kcur + 1: if it lies beyond this step and the
-            // next step's first edge, every lane stays in entry kcur
-            if (!kFast || (int64_t)__shfl_sync(kFull, sj, 0) <= es + 32) {  // warp-uniform
-                const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
-                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
-                const int c = __popc(starts & upto);
-                const int src_lane = c > 0 ? c - 1 : 0;
-                const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
-                const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
-                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
-                if (c > 0) {
-                    s_l = s_sh;
-                    b_l = b_sh;
-                    u_l = u_sh;  // taken before the walk advances
-                }
-                // advance to the entry holding the next step's first edge
-                // (at least one entry on the fast path)
-                const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
-                if (adv > 0) {
-                    scur = __shfl_sync(kFull, sj, adv - 1);
-                    bcur = __shfl_sync(kFull, bj, adv - 1);
-                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
-                    kcur += adv;
-                    fresh = false;
-                }
+            const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
+            const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
+            const int c = __popc(starts & upto);
+            const int src_lane = c > 0 ? c - 1 : 0;
+            const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
+            const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
+            const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
+            if (c > 0) {
+                s_l = s_sh;
+                b_l = b_sh;
+                u_l = u_sh;  // taken before the walk advances
+            }
+            // advance to the entry holding the next step's first edge
+            const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
+            if (adv > 0) {
+                scur = __shfl_sync(kFull, sj, adv - 1);
+                bcur = __shfl_sync(kFull, bj, adv - 1);
+                if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
+                kcur += adv;
+                fresh = false;
             }
             if (e < w1) {
                 const int64_t eidx = (int64_t)b_l + (e - (int64_t)s_l);
@@ -327,6 +380,7 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
         }
         relax_items<SSSP, STEPS, kOutNode, true, COH>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
                                                       err, wb, ws, cnt, o);
+        ew += 32 * STEPS;
     }
 }
 
