@@ -56,6 +56,28 @@ struct FlushOut {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// L2 prefetch hints: the lines are requested now and no register waits for
+// them, so a warp can have far more of its upcoming edges in flight than it
+// holds loads for.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// One bulk prefetch (cp.async.bulk.prefetch.L2) of the bytes [p, q) of an
+// array that ends at `limit`: the start is rounded down to 16 bytes and the
+// end rounded up but kept within the array's last whole 16 bytes.  Issued
+// by one thread.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, const void *q, const void *limit) {
+    const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
+    uintptr_t b = ((uintptr_t)q + 15) & ~(uintptr_t)15;
+    const uintptr_t lim = (uintptr_t)limit & ~(uintptr_t)15;
+    if (b > lim) b = lim;
+    if (b > a) {
+        const uint32_t bytes = (uint32_t)min((uintptr_t)(b - a), (uintptr_t)(1u << 20));
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+    }
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -219,7 +241,8 @@ __device__ __forceinline__ uint32_t ld_mut(const uint32_t *p) {
     return COH ? __ldcg(p) : *p;
 }
 
-template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false>
+// FLUSH = false: the caller flushes; then cnt + 32 * ITEMS <= kWB on entry.
+template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false, bool FLUSH = true>
 __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32_t (&vv)[ITEMS],
                                             const uint32_t (&ww)[ITEMS], const uint32_t (&dd)[ITEMS],
                                             const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
@@ -301,7 +324,7 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
     for (int it = 0; it < ITEMS; ++it) {
         const bool want = won[it] && ve[it] > vb[it];
         wpush(wb, cnt, want, vv[it], vb[it], (uint32_t)(ve[it] - vb[it]));
-        if (cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
+        if (FLUSH && cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
     }
 }
 

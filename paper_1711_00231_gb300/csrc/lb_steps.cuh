@@ -20,9 +20,12 @@
 #ifndef LB_WD_FAST_SSSP
 #define LB_WD_FAST_SSSP 1
 #endif
-// Edges a lane loads ahead in the run loop (more loads in flight per warp).
-#ifndef LB_WD_RUN_ITEMS
-#define LB_WD_RUN_ITEMS 2
+// L2 prefetch in the walk (bit mask): 1 = a BFS run's edge range with one
+// bulk prefetch, 2 = the first line of every look-ahead entry's adjacency
+// list.  Measured on R-MAT scale 24: 1 gains 2% on BFS (neutral for SSSP,
+// so SSSP does not use it), 2 costs 25-60% on levels with short lists.
+#ifndef LB_WD_PREFETCH
+#define LB_WD_PREFETCH 1
 #endif
 
 
@@ -261,11 +264,24 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
     // until the walk advances, so steps inside one long adjacency list
     // (most edges of a skewed graph) load no list entries at all
     constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
+    constexpr int R = STEPS;
+    static_assert(32 * R <= kWB / 2, "push buffer too small for one group");
     int32_t sj = INT32_MAX, bj = 0, uj = 0;
     bool fresh = false;
-    int64_t ew = w0;
+    // the walk produces one group of R x 32 edges per pass, either from a
+    // run (consecutive edges of entry kcur, loaded with a plain strided
+    // loop) or from the general step (entry boundaries inside the group),
+    // and relaxes every group at one call site
+    int64_t ew = w0;    // next list edge
+    int64_t rend = -1;  // end of the current run (exclusive); -1: no run
+    int64_t rbase = 0;  // edge id = rbase + list edge inside the run
+    bool radv = false;  // the run ends where entry kcur + 1 starts
+    uint32_t rdu = 0;   // SSSP: distance the run's source relaxes with
     while (ew < w1) {  // warp-uniform
-        if (!kFast || !fresh) {
+        int32_t vv[R];
+        uint32_t ww[R], dd[R];
+        bool ok[R];
+        if (!fresh) {
             const int64_t j = kcur + 1 + lane;
             sj = INT32_MAX;
             bj = 0;
@@ -274,113 +290,113 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
                 sj = ld_list<COH>(in.scan + j);
                 bj = ld_list<COH>(in.beg + j);
                 if (SSSP) uj = ld_list<COH>(in.v + j);
+                if ((LB_WD_PREFETCH & 2) && (uint32_t)bj < (uint64_t)g.m) {
+                    prefetch_l2(g.col + bj);
+                    if (SSSP) prefetch_l2(g.w + bj);
+                }
             }
             fresh = true;
         }
-        if (kFast) {
+        if (kFast && rend < 0) {
             // first edge of entry kcur + 1: when no entry starts inside the
             // next 32 edges, run through entry kcur's edges up to that start
-            // with a plain strided loop (no boundary search per step)
             const int64_t s_next = (int64_t)__shfl_sync(kFull, sj, 0);
             if (s_next > ew + 32) {
-                const int64_t rend = min(s_next, w1);
-                const int64_t base = (int64_t)bcur - (int64_t)scur;  // edge id = base + list edge
-                if (base + ew < 0 || base + rend > g.m) {
+                rend = min(s_next, w1);
+                radv = s_next <= w1;
+                rbase = (int64_t)bcur - (int64_t)scur;
+                if (rbase + ew < 0 || rbase + rend > g.m) {
                     if (lane == 0) atomicOr(err, kErrBounds);
                     return;
                 }
-                uint32_t du = 0;
-                if (SSSP) du = ld_mut<COH>(epoch + ucur) == stamp ? kInf : ld_mut<COH>(status + ucur);
-                constexpr int R = LB_WD_RUN_ITEMS;
-                for (int64_t x = ew; x < rend; x += 32 * R) {
-                    int32_t vv[R];
-                    uint32_t ww[R], dd[R];
-                    bool ok[R];
+                if ((LB_WD_PREFETCH & 1) && !SSSP && lane == 0 && rend - ew > 32 * R)
+                    bulk_prefetch_l2(g.col + (rbase + ew + 32 * R), g.col + (rbase + rend), g.col + g.m);
+                if (SSSP) rdu = ld_mut<COH>(epoch + ucur) == stamp ? kInf : ld_mut<COH>(status + ucur);
+            }
+        }
+        if (rend >= 0) {
 #pragma unroll
-                    for (int st = 0; st < R; ++st) {
-                        const int64_t e = x + 32 * st + lane;
-                        ok[st] = e < rend;
-                        vv[st] = ok[st] ? __ldg(g.col + (base + e)) : 0;
-                        ww[st] = (SSSP && ok[st]) ? __ldg(g.w + (base + e)) : 0u;
-                        dd[st] = du;
-                    }
-                    relax_items<SSSP, R, kOutNode, true, COH>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level,
-                                                              stamp, err, wb, ws, cnt, o);
-                }
-                ew = rend;
-                if (rend == s_next) {  // entry kcur + 1 starts at ew
-                    scur = (int32_t)s_next;
+            for (int st = 0; st < R; ++st) {
+                const int64_t e = ew + 32 * st + lane;
+                ok[st] = e < rend;
+                vv[st] = ok[st] ? __ldg(g.col + (rbase + e)) : 0;
+                ww[st] = (SSSP && ok[st]) ? __ldg(g.w + (rbase + e)) : 0u;
+                dd[st] = rdu;
+            }
+            ew = min(ew + 32 * R, rend);
+            if (ew == rend) {
+                if (radv) {  // entry kcur + 1 starts at ew
+                    scur = (int32_t)rend;
                     bcur = __shfl_sync(kFull, bj, 0);
                     if (SSSP) ucur = __shfl_sync(kFull, uj, 0);
                     kcur += 1;
                     fresh = false;
                 }
-                continue;
+                rend = -1;
             }
-        }
-        int32_t vv[STEPS];
-        uint32_t ww[STEPS], dd[STEPS];
-        bool ok[STEPS];
+        } else {
 #pragma unroll
-        for (int st = 0; st < STEPS; ++st) {
-            const int64_t es = ew + 32 * st;  // first edge of this step (uniform)
-            const int64_t e = es + lane;
-            ok[st] = false;
-            vv[st] = 0;
-            ww[st] = 0;
-            dd[st] = 0;
-            if (es >= w1) continue;  // warp-uniform
-            if (st > 0 && !fresh) {  // the previous step advanced: reload the window
-                const int64_t j = kcur + 1 + lane;
-                sj = INT32_MAX;
-                bj = 0;
-                uj = 0;
-                if (j < ihi) {
-                    sj = ld_list<COH>(in.scan + j);
-                    bj = ld_list<COH>(in.beg + j);
-                    if (SSSP) uj = ld_list<COH>(in.v + j);
+            for (int st = 0; st < R; ++st) {
+                const int64_t es = ew + 32 * st;  // first edge of this step (uniform)
+                const int64_t e = es + lane;
+                ok[st] = false;
+                vv[st] = 0;
+                ww[st] = 0;
+                dd[st] = 0;
+                if (es >= w1) continue;  // warp-uniform
+                if (!fresh) {  // the previous step advanced
+                    const int64_t j = kcur + 1 + lane;
+                    sj = INT32_MAX;
+                    bj = 0;
+                    uj = 0;
+                    if (j < ihi) {
+                        sj = ld_list<COH>(in.scan + j);
+                        bj = ld_list<COH>(in.beg + j);
+                        if (SSSP) uj = ld_list<COH>(in.v + j);
+                    }
+                    fresh = true;
                 }
-                fresh = true;
-            }
-            int32_t s_l = scur, b_l = bcur, u_l = ucur;
-            const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
-            const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
-            const int c = __popc(starts & upto);
-            const int src_lane = c > 0 ? c - 1 : 0;
-            const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
-            const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
-            const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
-            if (c > 0) {
-                s_l = s_sh;
-                b_l = b_sh;
-                u_l = u_sh;  // taken before the walk advances
-            }
-            // advance to the entry holding the next step's first edge
-            const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
-            if (adv > 0) {
-                scur = __shfl_sync(kFull, sj, adv - 1);
-                bcur = __shfl_sync(kFull, bj, adv - 1);
-                if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
-                kcur += adv;
-                fresh = false;
-            }
-            if (e < w1) {
-                const int64_t eidx = (int64_t)b_l + (e - (int64_t)s_l);
-                if ((uint64_t)eidx >= (uint64_t)g.m) {
-                    atomicOr(err, kErrBounds);
-                } else {
-                    ok[st] = true;
-                    vv[st] = __ldg(g.col + eidx);
-                    if (SSSP) {
-                        ww[st] = __ldg(g.w + eidx);
-                        dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
+                int32_t s_l = scur, b_l = bcur, u_l = ucur;
+                const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
+                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
+                const int c = __popc(starts & upto);
+                const int src_lane = c > 0 ? c - 1 : 0;
+                const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
+                const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
+                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
+                if (c > 0) {
+                    s_l = s_sh;
+                    b_l = b_sh;
+                    u_l = u_sh;  // taken before the walk advances
+                }
+                // advance to the entry holding the next step's first edge
+                const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
+                if (adv > 0) {
+                    scur = __shfl_sync(kFull, sj, adv - 1);
+                    bcur = __shfl_sync(kFull, bj, adv - 1);
+                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
+                    kcur += adv;
+                    fresh = false;
+                }
+                if (e < w1) {
+                    const int64_t eidx = (int64_t)b_l + (e - (int64_t)s_l);
+                    if ((uint64_t)eidx >= (uint64_t)g.m) {
+                        atomicOr(err, kErrBounds);
+                    } else {
+                        ok[st] = true;
+                        vv[st] = __ldg(g.col + eidx);
+                        if (SSSP) {
+                            ww[st] = __ldg(g.w + eidx);
+                            dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
+                        }
                     }
                 }
             }
+            ew += 32 * R;
         }
-        relax_items<SSSP, STEPS, kOutNode, true, COH>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
-                                                      err, wb, ws, cnt, o);
-        ew += 32 * STEPS;
+        if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
+        relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
+                                                         err, wb, ws, cnt, o);
     }
 }
 

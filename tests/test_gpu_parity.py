@@ -220,6 +220,26 @@ def test_device_created_graph_matches():
         lb.Graph(off, bad, None, g.n, g.m, device_arrays=True)
 
 
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_wd_with_unaligned_column_array(shift):
+    # the WD relax bulk-prefetches long adjacency lists into L2 in 16-byte
+    # units; a caller column array at any 4-byte offset (here through the
+    # entry point that works on caller device arrays) must give the same
+    # levels as the oracle
+    import torch
+    g = gg.rmat(14, 16, seed=3, weights=None)
+    src = gg.max_degree_vertex(g)
+    assert int(np.diff(g.offsets).max()) >= 1024   # long lists: runs with a bulk prefetch
+    off = torch.from_numpy(g.offsets).cuda()
+    buf = torch.zeros(g.m + 4, dtype=torch.int32, device="cuda")
+    col = buf[shift:shift + g.m]
+    col.copy_(torch.from_numpy(g.cols))
+    lev = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+    lb.lb_bfs_wd_noalloc(off, col, g.n, g.m, src, lev, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(lev.cpu().numpy(), oracle.bfs(g, src)[0])
+
+
 # ------------------------------------------------- schedule artefacts
 
 
