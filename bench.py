@@ -130,6 +130,21 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def stored_traffic(args):
+    """DRAM bytes per query of k_step_wd from the committed ncu capture of
+    this workload, if it was taken on the kernel build that runs now."""
+    path = os.path.join(ROOT, "profiles", "k_step_wd_traffic_rmat24_ef32.json")
+    if args.scale != 24 or args.edge_factor != 32 or args.wd_tile or not os.path.exists(path):
+        return None
+    from paper_1711_00231_gb300 import _build
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_digest") != _build.kernel_digest():
+        return None
+    d["file"] = "profiles/k_step_wd_traffic_rmat24_ef32.json"
+    return d
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -509,12 +524,19 @@ def main():
                      "work_inflation": sum(work[(kind, int(s))][4] for s in srcs) / max(
                          1, sum(work[(kind, int(s))][0] for s in srcs))}
     peak, peak_kind = measured_peak()
+    traffic = stored_traffic(args)
     dom = max(kinds, key=lambda k: per_query_ms[k].sum())
     achieved = res[dom]["algorithmic_gbs"]
     def roof(kind):
         a = res[kind]["algorithmic_gbs"]
+        t = traffic.get(kind) if traffic else None
         return {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
-                "traffic": None, "kernel": f"k_step_wd ({kind})", "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": t["dram_bytes_per_query"] if t else None,
+                "traffic_note": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum over all k_step_wd launches of "
+                                 f"one query from source 0 ({t['queries']} queries captured; algorithmic bytes of "
+                                 f"that query {t['algorithmic_bytes_per_query']:.4g}); {traffic['file']}")
+                if t else "no stored capture for this kernel build and workload",
+                "kernel": f"k_step_wd ({kind})", "peak_source": f"{peak_kind} hbm_gbs",
                 "unit_of_work": "one query (all its relax launches + set-up); algorithmic bytes per query "
                                 f"= {BYTES[kind][0]} B x m_reached + {BYTES[kind][1]} B x n_reached"}
     roofline = roof(dom)

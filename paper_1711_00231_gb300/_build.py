@@ -48,6 +48,21 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# the sources that define the WD relax kernel (k_step_wd) and its launch
+WD_KERNEL_SOURCES = ["lb_internal.cuh", "lb_device.cuh", "lb_steps.cuh", "lb_launch.h", "lb_step_wd.cu"]
+
+
+def kernel_digest() -> str:
+    """Digest of the WD relax kernel's sources and compile flags: a stored
+    profile of the kernel applies only while this is unchanged."""
+    h = hashlib.sha256()
+    h.update(" ".join(NVCC_FLAGS[:-3] + _extra_flags()).encode())  # flags without the include path
+    for f in WD_KERNEL_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link liblb.so unless an up-to-date build exists."""
     os.makedirs(BUILD, exist_ok=True)
