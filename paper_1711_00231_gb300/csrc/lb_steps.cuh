@@ -20,6 +20,19 @@
 #ifndef LB_WD_FAST_SSSP
 #define LB_WD_FAST_SSSP 1
 #endif
+// Column and weight streams loaded evict-first (ld.global.cs) so the
+// randomly read distance, stamp and visited lines keep their place in L2
+// (bit mask: 1 = SSSP, 2 = BFS).  Measured on R-MAT scale 24: SSSP 3.7%
+// faster, BFS unchanged.
+#ifndef LB_WD_STREAM
+#define LB_WD_STREAM 3
+#endif
+template <bool SSSP, class T>
+__device__ __forceinline__ T ld_edge(const T *p) {
+    constexpr bool kStream = (LB_WD_STREAM & (SSSP ? 1 : 2)) != 0;
+    return kStream ? __ldcs(p) : __ldg(p);
+}
+
 // L2 prefetch in the walk (bit mask): 1 = a BFS run's edge range with one
 // bulk prefetch, 2 = the first line of every look-ahead entry's adjacency
 // list.  Measured on R-MAT scale 24: 1 gains 2% on BFS (neutral for SSSP,
@@ -319,8 +332,8 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
             for (int st = 0; st < R; ++st) {
                 const int64_t e = ew + 32 * st + lane;
                 ok[st] = e < rend;
-                vv[st] = ok[st] ? __ldg(g.col + (rbase + e)) : 0;
-                ww[st] = (SSSP && ok[st]) ? __ldg(g.w + (rbase + e)) : 0u;
+                vv[st] = ok[st] ? ld_edge<SSSP>(g.col + (rbase + e)) : 0;
+                ww[st] = (SSSP && ok[st]) ? ld_edge<SSSP>(g.w + (rbase + e)) : 0u;
                 dd[st] = rdu;
             }
             ew = min(ew + 32 * R, rend);
@@ -384,9 +397,9 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
                         atomicOr(err, kErrBounds);
                     } else {
                         ok[st] = true;
-                        vv[st] = __ldg(g.col + eidx);
+                        vv[st] = ld_edge<SSSP>(g.col + eidx);
                         if (SSSP) {
-                            ww[st] = __ldg(g.w + eidx);
+                            ww[st] = ld_edge<SSSP>(g.w + eidx);
                             dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
                         }
                     }
