@@ -258,8 +258,10 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
         if (!ok[it]) continue;
         if (SSSP) {
             if (dd[it] == kInf) continue;
-            const uint64_t a64 = (uint64_t)dd[it] + (uint64_t)ww[it];
-            val[it] = a64 >= kSat ? kSat : (uint32_t)a64;
+            // dd + w saturated at kSat: a 32-bit sum that wrapped (s < dd) or
+            // reached kSat is exactly the case of the 64-bit sum >= kSat
+            const uint32_t s32 = dd[it] + ww[it];
+            val[it] = (s32 < dd[it] || s32 >= kSat) ? kSat : s32;
             cand[it] = val[it] < ld_mut<COH>(status + vv[it]);
         } else {
             cand[it] = !(ld_mut<COH>(bitmap + ((uint32_t)vv[it] >> 5)) & (1u << ((uint32_t)vv[it] & 31u)));
@@ -296,14 +298,15 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
         for (int it = 0; it < ITEMS; ++it)
             if (won[it] && prev[it] == stamp) won[it] = false;
     }
-    int64_t vb[ITEMS], ve[ITEMS];
+    // offsets are < m < 2^31 (checked when the graph is created)
+    int32_t vb[ITEMS], ve[ITEMS];
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
         vb[it] = 0;
         ve[it] = 0;
         if (won[it]) {
-            vb[it] = __ldg(off + vv[it]);
-            ve[it] = __ldg(off + vv[it] + 1);
+            vb[it] = (int32_t)__ldg(off + vv[it]);
+            ve[it] = (int32_t)__ldg(off + vv[it] + 1);
         }
     }
     if (KIND == kOutEdgesPerEdge) {

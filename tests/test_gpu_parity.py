@@ -175,6 +175,36 @@ def test_grid4096_sssp_from_corner():
         G.close()
 
 
+def test_rmat24_bench_workload():
+    # the bench's workload and launch configuration: R-MAT scale 24, edge
+    # factor 32, weights U[1,255], two of its 64 sources (seed 1), WD through
+    # the device loop.  BFS levels are compared with the oracle's BFS in
+    # full; SSSP distances pass the oracle's shortest-path certificate
+    # (dist[src] = 0, no edge improves a distance, every reached vertex has
+    # a tight in-edge), which holds only for the exact distances, and the
+    # first source's distances are also compared with Dijkstra in full.
+    import torch
+    g = gg.rmat(24, 32, seed=1)
+    srcs = gg.pick_sources(g, 64, seed=1)[:2].tolist()
+    G = lb.Graph.from_csr(g)
+    try:
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for i, src in enumerate(srcs):
+            G.bfs_dev(src, "WD", out)
+            torch.cuda.synchronize()
+            assert G.stats()["status"] == 0
+            assert np.array_equal(out.cpu().numpy(), oracle.bfs(g, src)[0]), src
+            G.sssp_dev(src, "WD", out)
+            torch.cuda.synchronize()
+            assert G.stats()["status"] == 0
+            d = out.cpu().numpy().view(np.uint32)
+            assert oracle.check_dist(g, src, d) == 0, src
+            if i == 0:
+                assert np.array_equal(d, oracle.dijkstra(g, src)[0])
+    finally:
+        G.close()
+
+
 def test_parents_are_valid_trees():
     import torch
     g = gg.rmat(14, 16, seed=3)
