@@ -6,6 +6,8 @@
 // replayed by a conditional WHILE node until the worklist is empty.
 #pragma once
 
+#include <type_traits>
+
 #include "lb_device.cuh"
 
 #ifndef LB_WD_MIN_BLOCKS
@@ -32,6 +34,12 @@ __device__ __forceinline__ T ld_edge(const T *p) {
     constexpr bool kStream = (LB_WD_STREAM & (SSSP ? 1 : 2)) != 0;
     return kStream ? __ldcs(p) : __ldg(p);
 }
+
+// BFS walks with 32-bit indices (wd_walk_tile32): 8% faster at R-MAT
+// scale 24 than the 64-bit walk.
+#ifndef LB_WD_IDX32
+#define LB_WD_IDX32 1
+#endif
 
 // L2 prefetch in the walk (bit mask): 1 = a BFS run's edge range with one
 // bulk prefetch, 2 = the first line of every look-ahead entry's adjacency
@@ -239,11 +247,191 @@ __device__ __forceinline__ T ld_list(const T *p) {
     return COH ? __ldcg(p) : __ldg(p);
 }
 
-// One tile of the walk.  COH selects L2-coherent loads for everything other
-// CTAs write (the persistent serving kernel); the single-query launches use
-// the read-only / L1 paths.
+// The walk of one tile with 32-bit list edges, list positions and edge
+// ids (all < 2^31, checked when the graph is created; edge-id arithmetic
+// wraps mod 2^32).  Used for BFS.
 template <bool SSSP, int STEPS, bool COH>
-__device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
+__device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
+                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
+                                             uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
+                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    const int64_t q = T / kTileGrain;
+    const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
+    const int64_t ntiles = (E + T - 1) / T;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
+    const int64_t e0 = t * T;
+    const int64_t e1 = min(e0 + T, E);
+    int64_t i0 = ld_list<COH>(in.tstart + t * q);
+    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)ld_list<COH>(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
+    if (i0 < 0 || i0 >= ihi) {
+        if (lane == 0) atomicOr(err, kErrBounds);
+        return;
+    }
+    using IT = uint32_t;  // list edges and edge ids
+    using KT = int32_t;   // list positions
+    const int64_t w064 = e0 + (int64_t)warp * W;
+    if (w064 >= e1) return;  // warp-uniform
+    const IT w0 = (IT)w064;
+    const IT w1 = (IT)min(w064 + W, e1);
+    const KT ihiK = (KT)ihi;
+    KT lo = (KT)i0, hi = ihiK;  // entry of the slice's first edge
+    while (hi - lo > 1) {
+        const KT mid = (KT)(((uint64_t)lo + (uint64_t)hi) >> 1);
+        if ((IT)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
+    }
+    KT kcur = lo;
+    int32_t scur = ld_list<COH>(in.scan + kcur);
+    int32_t bcur = ld_list<COH>(in.beg + kcur);
+    int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
+    // look-ahead window: lane l holds entry kcur + 1 + l; it stays valid
+    // until the walk advances, so steps inside one long adjacency list
+    // (most edges of a skewed graph) load no list entries at all
+    constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
+    constexpr int R = STEPS;
+    static_assert(32 * R <= kWB / 2, "push buffer too small for one group");
+    int32_t sj = INT32_MAX, bj = 0, uj = 0;
+    bool fresh = false;
+    // the walk produces one group of R x 32 edges per pass, either from a
+    // run (consecutive edges of entry kcur, loaded with a plain strided
+    // loop) or from the general step (entry boundaries inside the group),
+    // and relaxes every group at one call site
+    IT ew = w0;      // next list edge
+    IT rend = 0;     // end of the current run (exclusive)
+    IT rbase = 0;    // edge id = rbase + list edge inside the run
+    bool in_run = false;
+    bool radv = false;     // the run ends where entry kcur + 1 starts
+    uint32_t rdu = 0;      // SSSP: distance the run's source relaxes with
+    while (ew < w1) {  // warp-uniform
+        int32_t vv[R];
+        uint32_t ww[R], dd[R];
+        bool ok[R];
+        if (!fresh) {
+            const KT j = kcur + 1 + (KT)lane;
+            sj = INT32_MAX;
+            bj = 0;
+            uj = 0;
+            if (j < ihiK) {
+                sj = ld_list<COH>(in.scan + j);
+                bj = ld_list<COH>(in.beg + j);
+                if (SSSP) uj = ld_list<COH>(in.v + j);
+                if ((LB_WD_PREFETCH & 2) && (uint64_t)bj < (uint64_t)g.m) {
+                    prefetch_l2(g.col + bj);
+                    if (SSSP) prefetch_l2(g.w + bj);
+                }
+            }
+            fresh = true;
+        }
+        if (kFast && !in_run) {
+            // first edge of entry kcur + 1: when no entry starts inside the
+            // next 32 edges, run through entry kcur's edges up to that start
+            const IT s_next = (IT)__shfl_sync(kFull, sj, 0);
+            if (s_next > ew + 32) {
+                rend = s_next < w1 ? s_next : w1;
+                radv = s_next <= w1;
+                if ((int64_t)bcur + ((int64_t)ew - scur) < 0 || (int64_t)bcur + ((int64_t)rend - scur) > g.m) {
+                    if (lane == 0) atomicOr(err, kErrBounds);
+                    return;
+                }
+                rbase = (IT)bcur - (IT)scur;
+                in_run = true;
+                if ((LB_WD_PREFETCH & 1) && !SSSP && lane == 0 && rend - ew > (IT)(32 * R))
+                    bulk_prefetch_l2(g.col + (rbase + ew + (IT)(32 * R)), g.col + (rbase + rend), g.col + g.m);
+                if (SSSP) rdu = ld_mut<COH>(epoch + ucur) == stamp ? kInf : ld_mut<COH>(status + ucur);
+            }
+        }
+        if (in_run) {
+#pragma unroll
+            for (int st = 0; st < R; ++st) {
+                const IT e = ew + (IT)(32 * st) + (IT)lane;
+                ok[st] = e < rend;
+                vv[st] = ok[st] ? ld_edge<SSSP>(g.col + (rbase + e)) : 0;
+                ww[st] = (SSSP && ok[st]) ? ld_edge<SSSP>(g.w + (rbase + e)) : 0u;
+                dd[st] = rdu;
+            }
+            ew = ew + (IT)(32 * R) < rend ? ew + (IT)(32 * R) : rend;
+            if (ew == rend) {
+                if (radv) {  // entry kcur + 1 starts at ew
+                    scur = (int32_t)rend;
+                    bcur = __shfl_sync(kFull, bj, 0);
+                    if (SSSP) ucur = __shfl_sync(kFull, uj, 0);
+                    kcur += 1;
+                    fresh = false;
+                }
+                in_run = false;
+            }
+        } else {
+#pragma unroll
+            for (int st = 0; st < R; ++st) {
+                const IT es = ew + (IT)(32 * st);  // first edge of this step (uniform)
+                const IT e = es + (IT)lane;
+                ok[st] = false;
+                vv[st] = 0;
+                ww[st] = 0;
+                dd[st] = 0;
+                if (es >= w1) continue;  // warp-uniform
+                if (!fresh) {  // the previous step advanced
+                    const KT j = kcur + 1 + (KT)lane;
+                    sj = INT32_MAX;
+                    bj = 0;
+                    uj = 0;
+                    if (j < ihiK) {
+                        sj = ld_list<COH>(in.scan + j);
+                        bj = ld_list<COH>(in.beg + j);
+                        if (SSSP) uj = ld_list<COH>(in.v + j);
+                    }
+                    fresh = true;
+                }
+                int32_t s_l = scur, b_l = bcur, u_l = ucur;
+                const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es
+                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
+                const int c = __popc(starts & upto);
+                const int src_lane = c > 0 ? c - 1 : 0;
+                const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
+                const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
+                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
+                if (c > 0) {
+                    s_l = s_sh;
+                    b_l = b_sh;
+                    u_l = u_sh;  // taken before the walk advances
+                }
+                // advance to the entry holding the next step's first edge
+                const int adv = __popc(__ballot_sync(kFull, (IT)sj <= es + 32));
+                if (adv > 0) {
+                    scur = __shfl_sync(kFull, sj, adv - 1);
+                    bcur = __shfl_sync(kFull, bj, adv - 1);
+                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
+                    kcur += adv;
+                    fresh = false;
+                }
+                if (e < w1) {
+                    const IT eidx = (IT)b_l + (e - (IT)s_l);
+                    if ((uint64_t)eidx >= (uint64_t)g.m) {  // a wrapped 32-bit index is >= 2^31 > m
+                        atomicOr(err, kErrBounds);
+                    } else {
+                        ok[st] = true;
+                        vv[st] = ld_edge<SSSP>(g.col + eidx);
+                        if (SSSP) {
+                            ww[st] = ld_edge<SSSP>(g.w + eidx);
+                            dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
+                        }
+                    }
+                }
+            }
+            ew += (IT)(32 * R);
+        }
+        if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
+        relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
+                                                         err, wb, ws, cnt, o);
+    }
+}
+
+// The walk of one tile with 64-bit list edges and edge ids.  Used for SSSP:
+// its kernel runs slower with the 32-bit form of the same loop (22% at
+// R-MAT scale 24), and slower still with that loop at 64-bit width.
+template <bool SSSP, int STEPS, bool COH>
+__device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
                                              int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
                                              uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
                                              WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
@@ -411,6 +599,22 @@ __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &
         relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
                                                          err, wb, ws, cnt, o);
     }
+}
+
+// One tile of the walk.  COH selects L2-coherent loads for everything other
+// CTAs write (the persistent serving kernel); the single-query launches use
+// the read-only / L1 paths.
+template <bool SSSP, int STEPS, bool COH>
+__device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
+                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
+                                             uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
+                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    if constexpr (!SSSP && LB_WD_IDX32)
+        wd_walk_tile32<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, epoch, status, level, stamp, err, wb, ws,
+                                         cnt, o);
+    else
+        wd_walk_tile64<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, epoch, status, level, stamp, err, wb, ws,
+                                         cnt, o);
 }
 
 template <bool SSSP, int STEPS>
