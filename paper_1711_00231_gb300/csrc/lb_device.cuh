@@ -93,7 +93,12 @@ __device__ __forceinline__ uint32_t out_units(uint32_t deg, int32_t mdt) {
 }
 
 // Warp-uniform: every lane of the warp calls it with the same cnt.
-// Requires cnt + 32 <= kWB on entry.
+// Requires cnt + 32 <= kWB on entry.  The warp synchronises its buffer
+// writes here (LB_PUSH_SYNC = 1) or once at the start of the flush that
+// reads them (0).
+#ifndef LB_PUSH_SYNC
+#define LB_PUSH_SYNC 1
+#endif
 __device__ __forceinline__ void wpush(WarpBuf &b, uint32_t &cnt, bool want, int32_t v, int64_t beg, uint32_t deg) {
     // beg < m < 2^31: stored in 32 bits
     const unsigned m = __ballot_sync(kFull, want);
@@ -104,7 +109,7 @@ __device__ __forceinline__ void wpush(WarpBuf &b, uint32_t &cnt, bool want, int3
         b.deg[s] = deg;
     }
     cnt += __popc(m);
-    __syncwarp();
+    if (LB_PUSH_SYNC) __syncwarp();
 }
 
 // largest i in [0, n) with a[i] <= x (a[0] <= x assumed)
@@ -131,6 +136,7 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, ui
 template <int KIND, bool TILED>
 __device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
     if (cnt == 0) return;
+    if (!LB_PUSH_SYNC) __syncwarp();
     const uint32_t lane = lane_id();
     uint32_t run_u = 0, run_e = 0;
     for (uint32_t c = 0; c < cnt; c += 32) {
@@ -236,6 +242,12 @@ __device__ __forceinline__ uint32_t sssp_source_dist(const uint32_t *__restrict_
 // another (a warp-synchronous push between items would serialise them).
 // Loads of data other CTAs write: plain (L1) inside a single-iteration
 // launch, L2-coherent (ld.global.cg) inside the persistent serving kernel.
+// BFS visited check through L2 (1) instead of L1 (0): sees other SMs'
+// claims sooner at the cost of L2 latency (measured 31% slower at R-MAT
+// scale 24).
+#ifndef LB_BFS_BITMAP_CG
+#define LB_BFS_BITMAP_CG 0
+#endif
 template <bool COH>
 __device__ __forceinline__ uint32_t ld_mut(const uint32_t *p) {
     return COH ? __ldcg(p) : *p;
@@ -264,7 +276,7 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
             val[it] = (s32 < dd[it] || s32 >= kSat) ? kSat : s32;
             cand[it] = val[it] < ld_mut<COH>(status + vv[it]);
         } else {
-            cand[it] = !(ld_mut<COH>(bitmap + ((uint32_t)vv[it] >> 5)) & (1u << ((uint32_t)vv[it] & 31u)));
+            cand[it] = !(ld_mut<COH || LB_BFS_BITMAP_CG>(bitmap + ((uint32_t)vv[it] >> 5)) & (1u << ((uint32_t)vv[it] & 31u)));
         }
     }
     uint32_t prev[ITEMS];

@@ -290,7 +290,7 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
     // (most edges of a skewed graph) load no list entries at all
     constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
     constexpr int R = STEPS;
-    static_assert(32 * R <= kWB / 2, "push buffer too small for one group");
+    static_assert(32 * R <= kWB - 32, "push buffer too small for one group");
     int32_t sj = INT32_MAX, bj = 0, uj = 0;
     bool fresh = false;
     // the walk produces one group of R x 32 edges per pass, either from a
@@ -466,7 +466,7 @@ __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList
     // (most edges of a skewed graph) load no list entries at all
     constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
     constexpr int R = STEPS;
-    static_assert(32 * R <= kWB / 2, "push buffer too small for one group");
+    static_assert(32 * R <= kWB - 32, "push buffer too small for one group");
     int32_t sj = INT32_MAX, bj = 0, uj = 0;
     bool fresh = false;
     // the walk produces one group of R x 32 edges per pass, either from a
