@@ -7,7 +7,7 @@
 namespace lbk {
 
 #ifndef LB_WD_ITEMS
-#define LB_WD_ITEMS 2
+#define LB_WD_ITEMS 3
 #endif
 #ifndef LB_EP_ITEMS
 #define LB_EP_ITEMS 4
