@@ -130,6 +130,34 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def rank_sources(g, per_rank: int, rank: int, world: int):
+    """Rank r's sources: its slice of one seeded draw of per_rank x world
+    sources (uniform among out-degree > 0 vertices), so the ranks' query
+    sets are disjoint and together are the draw a single rank would make
+    for the whole job."""
+    import graphgen as gg
+    all_src = gg.pick_sources(g, per_rank * world, seed=1)
+    return all_src[rank * per_rank:(rank + 1) * per_rank]
+
+
+def combine_ranks(t_ms: float, edges_rank: float, world: int, device: str):
+    """Whole-job numbers over the ranks of a replica run: the slowest
+    rank's time, the edges every rank traversed, and GTEPS = total edges /
+    max time.  `device` is where the reduction tensors live ("cuda" under
+    NCCL, "cpu" under gloo)."""
+    edges_all = edges_rank
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        te = torch.tensor([edges_rank], device=device, dtype=torch.float64)
+        dist.all_reduce(te)
+        edges_all = float(te.item())
+    return t_ms, edges_all, edges_all / (t_ms / 1e3) / 1e9
+
+
 def stored_traffic(args):
     """DRAM bytes per query of k_step_wd from the committed ncu capture of
     this workload, if it was taken on the kernel build that runs now."""
@@ -413,8 +441,7 @@ def main():
     t0 = time.time()
     g = gg.rmat(args.scale, args.edge_factor, seed=1)
     t_gen = time.time() - t0
-    all_src = gg.pick_sources(g, args.sources * world, seed=1)
-    srcs = all_src[rank * args.sources:(rank + 1) * args.sources]
+    srcs = rank_sources(g, args.sources, rank, world)
     t0 = time.time()
     G = lb.Graph.from_csr(g)
     if args.loop_mode:
@@ -498,18 +525,8 @@ def main():
         trace_first[kind] = steps_first
     # device time of the queries themselves (the host sync between steps excluded)
     dev_ms = float(sum(per_query_ms[k].sum() for k in kinds))
-    t_ms = dev_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
     edges_rank = sum(work[(k, int(s))][0] for k in kinds for s in srcs) * args.steps
-    edges_all = edges_rank
-    if world > 1:
-        te = torch.tensor([edges_rank], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(te)
-        edges_all = float(te.item())
-    value = edges_all / (t_ms / 1e3) / 1e9
+    t_ms, edges_all, value = combine_ranks(dev_ms, edges_rank, world, "cuda")
 
     res = {}
     for kind in kinds:
