@@ -38,7 +38,12 @@ __device__ __forceinline__ T ld_edge(const T *p) {
 }
 
 // BFS walks with 32-bit indices (wd_walk_tile32): 8% faster at R-MAT
-// scale 24 than the 64-bit walk.
+// scale 24 than the 64-bit walk.  A run starts only where the current list
+// reaches more than LB_WD_RUN_MIN_BFS edges ahead (>= 32): shorter lists go
+// through boundary steps, whose groups are always full.
+#ifndef LB_WD_RUN_MIN_BFS
+#define LB_WD_RUN_MIN_BFS 32
+#endif
 #ifndef LB_WD_IDX32
 #define LB_WD_IDX32 1
 #endif
@@ -329,7 +334,7 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
             // first edge of entry kcur + 1: when no entry starts inside the
             // next 32 edges, run through entry kcur's edges up to that start
             const IT s_next = (IT)__shfl_sync(kFull, sj, 0);
-            if (s_next > ew + 32) {
+            if (s_next > ew + (IT)LB_WD_RUN_MIN_BFS) {
                 rend = s_next < w1 ? s_next : w1;
                 radv = s_next <= w1;
                 if ((int64_t)bcur + ((int64_t)ew - scur) < 0 || (int64_t)bcur + ((int64_t)rend - scur) > g.m) {
