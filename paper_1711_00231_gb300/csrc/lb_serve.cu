@@ -38,6 +38,7 @@ namespace srv {
 constexpr uint32_t kRing = 1u << 16;         // request / completion ring entries
 constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
 constexpr int kItems = 2;
+constexpr int kMaxSlots = 4096;
 constexpr uint64_t kAdmitPeriodNs = 50000;  // a busy CTA retries admission this often
 
 // Slot scheduling: 1 = round robin (after a tile a CTA moves on to the next
@@ -151,6 +152,7 @@ struct Shared {  // device-global control of the persistent kernel
     unsigned long long completed;
     unsigned long long kernel_t0;
     unsigned long long prof[8];  // per-phase cycle counters (LB_SERVE_PROFILE)
+    uint32_t busy_mask[kMaxSlots / 32];  // bit s: slot s holds a query (a scan hint)
 };
 
 struct Params {
@@ -283,6 +285,11 @@ __device__ void complete_query(const Params &P, Slot *S, int32_t status_code) {
     S->epoch_next = V->epoch_base + V->level + 1;
     const unsigned long long jw = atomicAdd(&S->job, 0ull);
     atomicExch(&S->job, job_word(job_gen(jw), kJobNone, 0u, 0u));
+    __threadfence();
+    // the slot's bit leaves the busy mask before the slot is released, so a
+    // later admission of the slot (which needs busy == 0) sets it again
+    const uint32_t si = (uint32_t)(S - P.slots);
+    atomicAnd(&P.sh->busy_mask[si >> 5], ~(1u << (si & 31u)));
     __threadfence();
     S->busy = 0;
     atomicSub(&P.sh->active, 1u);
@@ -457,6 +464,7 @@ __device__ void admit(const Params &P) {
         }
         S->busy = 1;
         atomicAdd(&sh->active, 1u);
+        atomicOr(&sh->busy_mask[(uint32_t)cursor >> 5], 1u << ((uint32_t)cursor & 31u));
         ++con;
         if (!valid) {
             complete_query(P, S, LB_ERR_ARG);
@@ -518,52 +526,67 @@ __global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
         __syncthreads();
         if (threadIdx.x == 0) PF_MARK(c_top);
         if (threadIdx.x < 32) {
-            // warp 0 looks at 32 slots per round: each lane reads one slot's
-            // claim word and job fields, and the claimable slots are tried in
-            // order until a claim holds (one L2 round trip per 32 slots)
+            // warp 0 reads up to 32 words of the busy mask in one L2 round
+            // trip, then for each word with busy slots (round robin from the
+            // slot after the one it last worked on, which itself comes first
+            // when this CTA just opened its next job) each lane reads one
+            // slot's claim and job words, and the claimable slots are tried
+            // in order until a claim holds
             const uint32_t lane = threadIdx.x;
             const uint32_t scan_from = s_scan_from;
+            const uint32_t nw = ((uint32_t)P.nslots + 31u) >> 5;
+            const uint32_t sw = scan_from >> 5;
             int found = -1;
             uint32_t f_kind = 0, f_tiles = 0, f_tile = 0, f_q = 0;
-            for (int32_t c0 = 0; c0 < P.nslots && found < 0; c0 += 32) {
-                const int32_t c = c0 + (int32_t)lane;
-                const int32_t si = (int32_t)((scan_from + (uint32_t)c) % (uint32_t)P.nslots);
-                bool claimable = false;
-                if (c < P.nslots) {
-                    const Slot *S = &P.slots[si];
-                    const unsigned long long w = __ldcg(&S->claim);
-                    const unsigned long long jw = __ldcg(&S->job);
-                    claimable = job_kind(jw) != kJobNone && job_gen(jw) == (uint32_t)(w >> 32) &&
-                                (uint32_t)w < job_tiles(jw);
-                }
-                unsigned cand = __ballot_sync(kFull, claimable);
-                while (cand) {
-                    const int l = __ffs(cand) - 1;
-                    cand &= cand - 1;
-                    int ok = 0;
-                    uint32_t k2 = 0, t2 = 0, q2 = 0, idx = 0;
-                    if ((int)lane == l) {
-                        Slot *S = &P.slots[si];
-                        const unsigned long long old = atomicAdd(&S->claim, 1ull);
-                        __threadfence();
-                        // the claim counts only if the job word still belongs to
-                        // the generation it was taken in (a late claim on a
-                        // finished job must not take a tile of the next job)
-                        const unsigned long long jw = atomicAdd(&S->job, 0ull);
-                        k2 = job_kind(jw);
-                        t2 = job_tiles(jw);
-                        q2 = job_q(jw);
-                        idx = (uint32_t)old;
-                        ok = job_gen(jw) == (uint32_t)(old >> 32) && k2 != kJobNone && idx < t2;
+            for (uint32_t base = 0; base < nw && found < 0; base += 32) {
+                uint32_t wmask = 0;
+                if (base + lane < nw) wmask = __ldcg(&P.sh->busy_mask[(sw + base + lane) % nw]);
+                unsigned nz = __ballot_sync(kFull, wmask != 0u);
+                while (nz && found < 0) {
+                    const int wl = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const uint32_t w = (sw + base + (uint32_t)wl) % nw;
+                    const uint32_t bits = __shfl_sync(kFull, wmask, wl);
+                    const uint32_t rot = (base == 0 && wl == 0) ? (scan_from & 31u) : 0u;
+                    const uint32_t sl = (lane + rot) & 31u;
+                    const int32_t si = (int32_t)(32u * w + sl);
+                    bool claimable = false;
+                    if (((bits >> sl) & 1u) && si < P.nslots) {
+                        const Slot *S = &P.slots[si];
+                        const unsigned long long cw = __ldcg(&S->claim);
+                        const unsigned long long jw = __ldcg(&S->job);
+                        claimable = job_kind(jw) != kJobNone && job_gen(jw) == (uint32_t)(cw >> 32) &&
+                                    (uint32_t)cw < job_tiles(jw);
                     }
-                    ok = __shfl_sync(kFull, ok, l);
-                    if (ok) {
-                        found = __shfl_sync(kFull, si, l);
-                        f_kind = __shfl_sync(kFull, k2, l);
-                        f_tiles = __shfl_sync(kFull, t2, l);
-                        f_q = __shfl_sync(kFull, q2, l);
-                        f_tile = __shfl_sync(kFull, idx, l);
-                        break;
+                    unsigned cand = __ballot_sync(kFull, claimable);
+                    while (cand) {
+                        const int l = __ffs(cand) - 1;
+                        cand &= cand - 1;
+                        int ok = 0;
+                        uint32_t k2 = 0, t2 = 0, q2 = 0, idx = 0;
+                        if ((int)lane == l) {
+                            Slot *S = &P.slots[si];
+                            const unsigned long long old = atomicAdd(&S->claim, 1ull);
+                            __threadfence();
+                            // the claim counts only if the job word still belongs
+                            // to the generation it was taken in (a late claim on a
+                            // finished job must not take a tile of the next job)
+                            const unsigned long long jw = atomicAdd(&S->job, 0ull);
+                            k2 = job_kind(jw);
+                            t2 = job_tiles(jw);
+                            q2 = job_q(jw);
+                            idx = (uint32_t)old;
+                            ok = job_gen(jw) == (uint32_t)(old >> 32) && k2 != kJobNone && idx < t2;
+                        }
+                        ok = __shfl_sync(kFull, ok, l);
+                        if (ok) {
+                            found = __shfl_sync(kFull, si, l);
+                            f_kind = __shfl_sync(kFull, k2, l);
+                            f_tiles = __shfl_sync(kFull, t2, l);
+                            f_q = __shfl_sync(kFull, q2, l);
+                            f_tile = __shfl_sync(kFull, idx, l);
+                            break;
+                        }
                     }
                 }
             }
@@ -822,7 +845,7 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     if (o.tile == 0) o.tile = 8192;
     if (o.idle_us == 0) o.idle_us = 1000;
     if (o.mem_fraction <= 0.0) o.mem_fraction = 0.5;
-    if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > 4096 || o.idle_us < 0 ||
+    if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > kMaxSlots || o.idle_us < 0 ||
         o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32) {
         delete s;
         return sfail(LB_ERR_ARG, "bad server options");
