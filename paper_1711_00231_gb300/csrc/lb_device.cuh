@@ -133,12 +133,16 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, ui
 #else
 #define LB_FLUSH_INLINE inline
 #endif
-template <int KIND, bool TILED>
-__device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
-    if (cnt == 0) return;
-    if (!LB_PUSH_SYNC) __syncwarp();
+// The two halves of a flush: the warp's exclusive prefix of output units and
+// edges over its buffered entries (into `s`), and the writes at the list
+// position / edge prefix `old` (packed entries << 32 | edges) reserved for
+// them.
+template <int KIND>
+__device__ __forceinline__ void wflush_prefix(const WarpBuf &b, WarpScratch &s, uint32_t cnt, const FlushOut &o,
+                                              uint32_t &run_u, uint32_t &run_e) {
     const uint32_t lane = lane_id();
-    uint32_t run_u = 0, run_e = 0;
+    run_u = 0;
+    run_e = 0;
     for (uint32_t c = 0; c < cnt; c += 32) {
         const uint32_t i = c + lane;
         const uint32_t d = i < cnt ? b.deg[i] : 0u;
@@ -154,10 +158,12 @@ __device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt
         run_u += __shfl_sync(kFull, iu, 31);
         run_e += __shfl_sync(kFull, ie, 31);
     }
-    unsigned long long old = 0;
-    if (lane == 0) old = atomicAdd(o.pack, ((unsigned long long)run_u << 32) | (unsigned long long)run_e);
-    old = __shfl_sync(kFull, old, 0);
-    __syncwarp();
+}
+
+template <int KIND, bool TILED>
+__device__ __forceinline__ void wflush_write(const WarpBuf &b, const WarpScratch &s, uint32_t &cnt, const FlushOut &o,
+                                             unsigned long long old, uint32_t run_u) {
+    const uint32_t lane = lane_id();
     const int64_t ubase = (int64_t)(old >> 32);
     const int64_t ebase = (int64_t)(old & 0xFFFFFFFFull);
     if (ubase + (int64_t)run_u > o.cap) {
@@ -194,9 +200,56 @@ __device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt
             }
         }
     }
-    if (lane == 0) atomicAdd(o.pushes, (unsigned long long)run_u);
     cnt = 0;
     __syncwarp();
+}
+
+template <int KIND, bool TILED>
+__device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
+    if (cnt == 0) return;
+    if (!LB_PUSH_SYNC) __syncwarp();
+    const uint32_t lane = lane_id();
+    uint32_t run_u, run_e;
+    wflush_prefix<KIND>(b, s, cnt, o, run_u, run_e);
+    unsigned long long old = 0;
+    if (lane == 0) {
+        old = atomicAdd(o.pack, ((unsigned long long)run_u << 32) | (unsigned long long)run_e);
+        atomicAdd(o.pushes, (unsigned long long)run_u);
+    }
+    old = __shfl_sync(kFull, old, 0);
+    __syncwarp();
+    wflush_write<KIND, TILED>(b, s, cnt, o, old, run_u);
+}
+
+// Block-wide flush of every warp's buffer (every thread of the block calls
+// it): one list reservation per CTA instead of one per warp.  At the end of
+// an iteration every warp with pushes flushes at once, and on lists with
+// many small pushes (a grid's SSSP wavefront) thousands of same-address
+// atomics per iteration would queue at one L2 slice.  The packed add is
+// exact: a list's entries and its edges (< m < 2^31) each fit their half.
+template <int KIND, bool TILED>
+__device__ void wflush_block(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
+    __shared__ unsigned long long s_tot[kWarps];
+    __shared__ unsigned long long s_base;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    __syncwarp();
+    uint32_t run_u = 0, run_e = 0;
+    if (cnt) wflush_prefix<KIND>(b, s, cnt, o, run_u, run_e);
+    if (lane == 0) s_tot[warp] = ((unsigned long long)run_u << 32) | (unsigned long long)run_e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long sum = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const unsigned long long t = s_tot[w];
+            s_tot[w] = sum;
+            sum += t;
+        }
+        s_base = sum ? atomicAdd(o.pack, sum) : 0ull;
+        if (sum) atomicAdd(o.pushes, sum >> 32);
+    }
+    __syncthreads();
+    if (cnt) wflush_write<KIND, TILED>(b, s, cnt, o, s_base + s_tot[warp], run_u);
+    cnt = 0;
 }
 
 // ---- relax ops ------------------------------------------------------------

@@ -414,7 +414,11 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t q, WarpB
     wd_walk_tile<SSSP, kItems, true>(g, S->lists[st.par], st.in_cnt, (int64_t)st.in_edges, q * kTileGrain, t,
                                      S->bitmap, S->epoch, st.status, st.level, st.epoch_base + st.level, &S->error, wb,
                                      ws, cnt, o);
+#if LB_BLOCK_FLUSH
+    wflush_block<kOutNode, true>(wb, ws, cnt, o);
+#else
     wflush<kOutNode, true>(wb, ws, cnt, o);
+#endif
 }
 
 // ---- admission -------------------------------------------------------------

@@ -48,6 +48,12 @@ __device__ __forceinline__ T ld_edge(const T *p) {
 #define LB_WD_IDX32 1
 #endif
 
+// The final flush of a WD iteration (and of a serving RELAX tile) as one
+// list reservation per CTA (wflush_block) instead of one per warp.
+#ifndef LB_BLOCK_FLUSH
+#define LB_BLOCK_FLUSH 1
+#endif
+
 // L2 prefetch in the walk (bit mask): 1 = a BFS run's edge range with one
 // bulk prefetch, 2 = the first line of every look-ahead entry's adjacency
 // list.  Measured on R-MAT scale 24: 1 gains 2% on BFS (neutral for SSSP,
@@ -660,7 +666,11 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
     wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
+#if LB_BLOCK_FLUSH
+    wflush_block<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
+#else
     wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
+#endif
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }
 
