@@ -54,6 +54,12 @@ __device__ __forceinline__ T ld_edge(const T *p) {
 #define LB_BLOCK_FLUSH 1
 #endif
 
+// Warp-wide 32-way search for a warp's first list entry (bit mask: 1 = the
+// BFS walk, 2 = the SSSP walk) instead of a per-warp binary search.
+#ifndef LB_WD_WARP_SEARCH
+#define LB_WD_WARP_SEARCH 3
+#endif
+
 // L2 prefetch in the walk (bit mask): 1 = a BFS run's edge range with one
 // bulk prefetch, 2 = the first line of every look-ahead entry's adjacency
 // list.  Measured on R-MAT scale 24: 1 gains 2% on BFS (neutral for SSSP,
@@ -260,6 +266,23 @@ __device__ __forceinline__ T ld_list(const T *p) {
     return COH ? __ldcg(p) : __ldg(p);
 }
 
+// The list entry holding list edge w0 within [lo, hi) (scan[lo] <= w0 <
+// scan[hi], hi may be the end): a warp-wide 32-way search, 31 probes per
+// round and a ballot, so a range of up to 32^k entries takes k rounds of
+// one load latency each instead of k * 5 dependent loads.
+template <bool COH, class IT, class KT>
+__device__ __forceinline__ KT warp_search(const int32_t *scan, KT lo, KT hi, IT w0, uint32_t lane) {
+    while (hi - lo > 1) {  // warp-uniform
+        const KT step = (hi - lo + 31) / 32;
+        const KT p = lo + step * (KT)(lane + 1);
+        const bool le = p < hi && (IT)ld_list<COH>(scan + p) <= w0;
+        const KT n = (KT)__popc(__ballot_sync(kFull, le));  // probes are increasing: a prefix of lanes
+        lo += step * n;
+        if (lo + step < hi) hi = lo + step;
+    }
+    return lo;
+}
+
 // The walk of one tile with 32-bit list edges, list positions and edge
 // ids (all < 2^31, checked when the graph is created; edge-id arithmetic
 // wraps mod 2^32).  Used for BFS.
@@ -289,12 +312,15 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
     const IT w0 = (IT)w064;
     const IT w1 = (IT)min(w064 + W, e1);
     const KT ihiK = (KT)ihi;
-    KT lo = (KT)i0, hi = ihiK;  // entry of the slice's first edge
-    while (hi - lo > 1) {
-        const KT mid = (KT)(((uint64_t)lo + (uint64_t)hi) >> 1);
-        if ((IT)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
+    KT kcur = (LB_WD_WARP_SEARCH & 1) ? warp_search<COH, IT, KT>(in.scan, (KT)i0, ihiK, w0, lane) : (KT)i0;
+    if (!(LB_WD_WARP_SEARCH & 1)) {
+        KT lo = (KT)i0, hi = ihiK;  // entry of the slice's first edge
+        while (hi - lo > 1) {
+            const KT mid = (KT)(((uint64_t)lo + (uint64_t)hi) >> 1);
+            if ((IT)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
+        }
+        kcur = lo;
     }
-    KT kcur = lo;
     int32_t scur = ld_list<COH>(in.scan + kcur);
     int32_t bcur = ld_list<COH>(in.beg + kcur);
     int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
@@ -465,12 +491,17 @@ __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList
     const int64_t w0 = e0 + (int64_t)warp * W;
     const int64_t w1 = min(w0 + W, e1);
     if (w0 >= w1) return;  // warp-uniform
-    int64_t lo = i0, hi = ihi;  // entry of the slice's first edge
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
+    int64_t kcur = i0;
+    if (LB_WD_WARP_SEARCH & 2) {
+        kcur = warp_search<COH, int64_t, int64_t>(in.scan, i0, ihi, w0, lane);
+    } else {
+        int64_t lo = i0, hi = ihi;  // entry of the slice's first edge
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
+        }
+        kcur = lo;
     }
-    int64_t kcur = lo;
     int32_t scur = ld_list<COH>(in.scan + kcur);
     int32_t bcur = ld_list<COH>(in.beg + kcur);
     int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
