@@ -307,6 +307,9 @@ def grid_bench(torch):
         row[f"{kind}_iterations"] = st["iterations"]
         row[f"{kind}_us_per_iteration"] = 1e3 * a.elapsed_time(b) / max(1, st["iterations"])
         row[f"{kind}_gteps"] = g.m / (a.elapsed_time(b) / 1e3) / 1e9
+        row[f"{kind}_edges_relaxed"] = st["edges_relaxed"]
+        row[f"{kind}_work_inflation"] = st["edges_relaxed"] / g.m
+        row[f"{kind}_edges_per_iteration"] = st["edges_relaxed"] / max(1, st["iterations"])
     S = sv.Server([G], slots=4)
     for kind in ("bfs", "sssp"):
         S.run_batch([sv.Request(0.0, 0, 0, kind)], [out])
