@@ -37,7 +37,15 @@ namespace srv {
 
 constexpr uint32_t kRing = 1u << 16;         // request / completion ring entries
 constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
-constexpr int kItems = 2;
+// edges per thread per round in a RELAX tile, and CTAs per SM the kernel is
+// compiled for (the register budget)
+#ifndef LB_SERVE_ITEMS
+#define LB_SERVE_ITEMS 2
+#endif
+#ifndef LB_SERVE_MIN_BLOCKS
+#define LB_SERVE_MIN_BLOCKS 4
+#endif
+constexpr int kItems = LB_SERVE_ITEMS;
 constexpr int kMaxSlots = 4096;
 constexpr uint64_t kAdmitPeriodNs = 50000;  // a busy CTA retries admission this often
 
@@ -502,7 +510,7 @@ __device__ void release_admit(const Params &P) {
 
 // ---- the persistent kernel -------------------------------------------------
 
-__global__ void __launch_bounds__(kBlock, 4) k_serve(Params P) {
+__global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
     __shared__ int s_slot;
