@@ -251,6 +251,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def small_configs(torch, reps: int = 3):
+    """The two smaller R-MAT configurations, every strategy: scale 14 (edge
+    factor 16, BFS from vertex 0) and scale 20 (edge factor 16, weights
+    U[1,255], BFS and SSSP from the highest-degree vertex).  ms per query
+    (mean of `reps` warm runs, CUDA events) and GTEPS = m_reached / time."""
+    import graphgen as gg
+    from paper_1711_00231_gb300 import lb
+    out = {}
+    g20 = gg.rmat(20, 16, seed=1)
+    for name, g, src, kinds in (("rmat14_ef16_vertex0", gg.rmat(14, 16, seed=1), 0, ("bfs",)),
+                                ("rmat20_ef16_maxdeg", g20, gg.max_degree_vertex(g20), ("bfs", "sssp"))):
+        G = lb.Graph.from_csr(g)
+        buf = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        deg = np.diff(g.offsets)
+        row = {"n": g.n, "m": g.m, "source": int(src)}
+        for kind in kinds:
+            f = G.bfs_dev if kind == "bfs" else G.sssp_dev
+            for s_name in ("BS", "EP", "WD", "NS", "HP", "NS_PHYS"):
+                f(int(src), s_name, buf)
+                torch.cuda.synchronize()
+                res = buf.cpu().numpy()
+                reached = res >= 0 if kind == "bfs" else res.view(np.uint32) != 0xFFFFFFFF
+                m_r = int(deg[reached].sum())
+                tot = 0.0
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    f(int(src), s_name, buf)
+                    b.record()
+                    torch.cuda.synchronize()
+                    tot += a.elapsed_time(b)
+                ms = tot / reps
+                row[f"{kind}_{s_name}"] = {"ms": ms, "gteps": m_r / (ms / 1e3) / 1e9}
+        G.close()
+        out[name] = row
+    return out
+
+
 def chunking_ablation(torch, sources: int = 4):
     """The paper's Sec. IV-D experiment on an rmat20-shaped graph (R-MAT
     scale 20, edge factor 16): EP with work chunking (one reservation for all
@@ -587,6 +625,7 @@ def main():
             extra[kind] = row
         G.release()
         extra["chunking_ablation"] = chunking_ablation(torch)
+        extra["configs"] = small_configs(torch)
         extra["grid4096"] = grid_bench(torch)
 
     # end to end through the host-buffer C-ABI calls (lb_bfs / lb_sssp):
