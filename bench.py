@@ -268,7 +268,9 @@ def small_configs(torch, reps: int = 3):
         row = {"n": g.n, "m": g.m, "source": int(src)}
         for kind in kinds:
             f = G.bfs_dev if kind == "bfs" else G.sssp_dev
-            for s_name in ("BS", "EP", "WD", "NS", "HP", "NS_PHYS"):
+            for label in ("BS", "EP", "WD", "NS", "HP", "HP_binned", "NS_PHYS"):
+                s_name = "HP" if label == "HP_binned" else label
+                G.set_options(hp_mode=1 if label == "HP_binned" else 0)
                 f(int(src), s_name, buf)
                 torch.cuda.synchronize()
                 res = buf.cpu().numpy()
@@ -283,7 +285,7 @@ def small_configs(torch, reps: int = 3):
                     torch.cuda.synchronize()
                     tot += a.elapsed_time(b)
                 ms = tot / reps
-                row[f"{kind}_{s_name}"] = {"ms": ms, "gteps": m_r / (ms / 1e3) / 1e9}
+                row[f"{kind}_{label}"] = {"ms": ms, "gteps": m_r / (ms / 1e3) / 1e9}
         G.close()
         out[name] = row
     return out
@@ -605,7 +607,10 @@ def main():
         cmp_src = srcs[:args.compare_sources]
         for kind in kinds:
             row = {}
-            for s_name in ("BS", "EP", "WD", "NS", "HP"):
+            for label in ("BS", "EP", "WD", "NS", "HP", "HP_binned"):
+                # HP_binned: HP with hp_mode 1 (degree-binned sub-worklists in one step)
+                s_name = "HP" if label == "HP_binned" else label
+                G.set_options(hp_mode=1 if label == "HP_binned" else 0)
                 tot = 0.0
                 e_tot = 0
                 for s in cmp_src:
@@ -619,7 +624,8 @@ def main():
                     tot += a.elapsed_time(b)
                     e_tot += work[(kind, int(s))][0]
                     assert G.stats()["status"] == 0
-                row[s_name] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9}
+                row[label] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9}
+            G.set_options(hp_mode=0)
             row["speedup_wd_vs_bs"] = row["BS"]["ms_per_query"] / row["WD"]["ms_per_query"]
             row["speedup_wd_vs_ep"] = row["EP"]["ms_per_query"] / row["WD"]["ms_per_query"]
             extra[kind] = row

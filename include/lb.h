@@ -93,7 +93,17 @@ typedef struct lb_options {
                               gives every CTA about two tiles */
     int32_t ctas_per_sm;   /* CTAs per SM the fixed relax grid is sized for;
                               0 = the occupancy limit */
-    int32_t reserved[10];
+    int32_t hp_mode;       /* HP form: 0 = the paper's sub-iterations (Sec.
+                              III-C: every node relaxes at most MDT edges per
+                              sub-iteration, unfinished nodes form the next
+                              sub-list); 1 = one step per super-iteration
+                              with the list's nodes binned by degree into
+                              sub-worklists served by a thread (<= min(MDT,
+                              32) edges), a warp (<= hp_warp_max) or the
+                              whole CTA (more) (0) */
+    int32_t hp_warp_max;   /* hp_mode 1: largest degree a warp serves; larger
+                              nodes go to the CTA bin (4096) */
+    int32_t reserved[8];
 } lb_options;
 
 /* Device bytes by structure (lb_mem_report).  "extra" is everything a
@@ -137,7 +147,8 @@ typedef struct lb_query_stats {
 /* One kernel step of the last query (lb_last_trace). */
 typedef struct lb_step_record {
     int32_t level;         /* super-iteration (BFS level of the list) */
-    int32_t mode;          /* 0 relax, 1 HP sub-iteration, 2 HP WD step */
+    int32_t mode;          /* 0 relax, 1 HP sub-iteration, 2 HP WD step,
+                              3 HP degree-binned step (hp_mode 1) */
     int64_t list_size;     /* entries in the list this step consumed */
     int64_t edges;         /* edges relaxed by this step */
     int64_t t_ns;          /* device time at the end of the step, in ns from

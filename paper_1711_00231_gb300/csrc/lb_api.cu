@@ -172,6 +172,8 @@ lb_options default_options() {
     o.hist_bins = 10;
     o.mdt_override = 0;
     o.hp_threshold = 1024;
+    o.hp_mode = 0;
+    o.hp_warp_max = 4096;
     o.loop_mode = 0;
     o.wd_tile = 8192;
     o.ctas_per_sm = 0;
@@ -183,6 +185,9 @@ lb_status normalise_options(const lb_options *in, lb_options *out) {
     lb_options o = *in;
     if (o.hist_bins == 0) o.hist_bins = d.hist_bins;
     if (o.hp_threshold == 0) o.hp_threshold = d.hp_threshold;
+    if (o.hp_warp_max == 0) o.hp_warp_max = d.hp_warp_max;
+    if (o.hp_mode != 0 && o.hp_mode != 1) return fail(LB_ERR_ARG, "hp_mode must be 0 or 1");
+    if (o.hp_warp_max < 32) return fail(LB_ERR_ARG, "hp_warp_max must be >= 32");
     if (o.wd_tile == 0) o.wd_tile = d.wd_tile;
     if (o.hist_bins < 1 || o.hist_bins > 4096) return fail(LB_ERR_ARG, "hist_bins must be in [1, 4096]");
     if (o.mdt_override < 0) return fail(LB_ERR_ARG, "mdt_override must be >= 0");
@@ -377,6 +382,8 @@ StepParams make_params(const lb_graph *g, int s) {
     p.tile = g->opt.wd_tile;
     p.mdt = (int32_t)(g->mdt > 0 ? g->mdt : 1);
     p.hp_threshold = g->opt.hp_threshold;
+    p.hp_mode = g->opt.hp_mode;
+    p.hp_warp_max = g->opt.hp_warp_max;
     p.strategy = s;
     p.use_cond = 0;
     return p;

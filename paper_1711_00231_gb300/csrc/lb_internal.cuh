@@ -42,7 +42,7 @@ enum : uint32_t {
 };
 
 // step modes recorded in the trace
-enum : int32_t { kModeRelax = 0, kModeHpSub = 1, kModeHpWd = 2 };
+enum : int32_t { kModeRelax = 0, kModeHpSub = 1, kModeHpWd = 2, kModeHpBin = 3 };
 
 // which list an HP step reads
 enum : uint32_t { kHpFromSuper = 0, kHpFromSub = 1 };
@@ -68,7 +68,7 @@ struct Ctl {
     uint64_t in_edges;  // edges of the input list (sum of entry lengths)
     unsigned long long out_pack;  // output list: (entries << 32) | edges
     unsigned long long sub_pack;  // HP sub-list output: (entries << 32) | edges
-    uint32_t hp_kind;   // HP: next step is a sub-iteration (1) or WD (2)
+    uint32_t hp_kind;   // HP: next step is a sub-iteration (1), WD (2) or binned (3)
     uint32_t hp_sub;    // HP: sub-iteration index inside the super-iteration
     uint32_t sub_in;    // HP: sub list buffer read when hp_from == kHpFromSub
     uint32_t blocks_done;
@@ -125,6 +125,8 @@ struct StepParams {
     int32_t tile;       // largest tile (edges) an iteration may use
     int32_t mdt;
     int32_t hp_threshold;  // <= 0: never switch to WD
+    int32_t hp_mode;       // 0: sub-iterations, 1: degree-binned steps
+    int32_t hp_warp_max;   // hp_mode 1: largest degree a warp serves
     int32_t strategy;
     int32_t use_cond;
     int32_t pad;

@@ -777,6 +777,32 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
 // the threshold, one workload-decomposition step over everything left.
 // Nodes updated in any step go to the next super worklist.
 // ---------------------------------------------------------------------------
+// Edges first + lane + k * stride (< last) of one node, relaxed ITEMS per
+// lane at a time from source distance du (the warp and CTA bins of the
+// degree-binned HP step).  first, last and stride are warp-uniform.
+template <bool SSSP, int ITEMS>
+__device__ __forceinline__ void serve_range(const StepParams &p, Ctl *ctl, int64_t first, int64_t last, int64_t stride,
+                                            uint32_t du, uint32_t *status, uint32_t level, uint32_t stamp,
+                                            WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    const uint32_t lane = lane_id();
+    for (int64_t e0 = first; e0 < last; e0 += stride * ITEMS) {
+        bool ok[ITEMS];
+        int32_t vv[ITEMS];
+        uint32_t ww[ITEMS], dd[ITEMS];
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const int64_t e = e0 + (int64_t)it * stride + lane;
+            ok[it] = e < last;
+            vv[it] = ok[it] ? __ldg(p.g.col + e) : 0;
+            ww[it] = (SSSP && ok[it]) ? __ldg(p.g.w + e) : 0u;
+            dd[it] = du;
+        }
+        if (cnt > kWB - 32 * ITEMS) wflush<kOutNode, true>(wb, ws, cnt, o);
+        relax_items<SSSP, ITEMS, kOutNode, true, false, false>(ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status,
+                                                              level, stamp, &ctl->error, wb, ws, cnt, o);
+    }
+}
+
 __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
     __threadfence();
     const unsigned long long pk = ld_volatile(&ctl->out_pack);
@@ -786,7 +812,7 @@ __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
     if (sub_cnt > p.list_cap) { ctl->error |= kErrCapacity; sub_cnt = p.list_cap; }
     const uint32_t kind = ctl->hp_kind;
     const int64_t step_edges = kind == 1u ? (int64_t)ctl->in_edges - sub_edges : (int64_t)ctl->in_edges;
-    trace_append(ctl, kind == 1u ? kModeHpSub : kModeHpWd, ctl->in_cnt, step_edges);
+    trace_append(ctl, kind == 1u ? kModeHpSub : (kind == 3u ? kModeHpBin : kModeHpWd), ctl->in_cnt, step_edges);
     ctl->relaxed += (unsigned long long)step_edges;
     ctl->step += 1;
     ctl->blocks_done = 0;
@@ -816,7 +842,7 @@ __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
         ctl->level += 1;
         ctl->hp_from = kHpFromSuper;
         ctl->hp_sub = 0;
-        ctl->hp_kind = (thr > 0 && cnt < thr) ? 2u : 1u;
+        ctl->hp_kind = (thr > 0 && cnt < thr) ? 2u : (p.hp_mode == 1 ? 3u : 1u);
         set_loop(p, ctl, cnt > 0);
     }
     __threadfence();
@@ -858,6 +884,85 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     uint32_t cnt = 0, scnt = 0;
     if (kind == 2u) {
         wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
+    } else if (kind == 3u) {
+        // Degree-binned step (hp_mode 1): the list's nodes are binned by
+        // degree into sub-worklists and all of them are served in this one
+        // step -- a node of at most min(MDT, 32) edges by its own thread, one of at
+        // most hp_warp_max edges by its warp (the warp takes its class-1
+        // nodes one after another), a larger one by the whole CTA after the
+        // block's batches (the CTA bin is a block-local list; when it is full
+        // the warp serves the node instead).
+        constexpr int kBigCap = 256;
+        __shared__ int32_t s_big[kBigCap];
+        __shared__ uint32_t s_nbig;
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+        // a thread serves at most 32 edges (fewer when MDT is smaller): on a
+        // skewed graph the histogram MDT runs into the thousands
+        const int64_t tmax = p.mdt < 32 ? (int64_t)p.mdt : 32;
+        const int64_t wmax = p.hp_warp_max;
+        const int64_t stride = (int64_t)gridDim.x * kBlock;
+        for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
+            const int64_t i = base + lane;
+            int64_t cur = 0, len = 0;
+            uint32_t du = 0;
+            int cls = -1;  // -1 nothing to do, 0 thread, 1 warp, 2 CTA
+            if (i < in_cnt) {
+                cur = __ldg(in.beg + i);
+                len = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
+                if (cur < 0 || len < 0 || cur + len > p.g.m) {
+                    atomicOr(&ctl->error, kErrBounds);
+                } else {
+                    if (SSSP) du = sssp_source_dist(status, p.epoch, __ldg(in.v + i), stamp);
+                    if (!SSSP || du != kInf) cls = len <= tmax ? 0 : (len <= wmax ? 1 : 2);
+                }
+            }
+            if (cls == 2) {
+                const uint32_t slot = atomicAdd(&s_nbig, 1u);
+                if (slot < (uint32_t)kBigCap) s_big[slot] = (int32_t)i;
+                else cls = 1;
+            }
+            unsigned wm = __ballot_sync(kFull, cls == 1);
+            while (wm) {
+                const int l = __ffs(wm) - 1;
+                wm &= wm - 1;
+                const int64_t c0 = __shfl_sync(kFull, cur, l);
+                const int64_t n0 = __shfl_sync(kFull, len, l);
+                const uint32_t d0 = __shfl_sync(kFull, du, l);
+                serve_range<SSSP, ITEMS>(p, ctl, c0, c0 + n0, 32, d0, status, level, stamp, wb, ws, cnt, osup);
+            }
+            int64_t end = cls == 0 ? cur + len : cur;
+            while (__any_sync(kFull, cur < end)) {
+                bool want = false;
+                int32_t v = 0;
+                int64_t vb = 0;
+                uint32_t vd = 0;
+                if (cur < end) {
+                    v = __ldg(p.g.col + cur);
+                    const bool hit = SSSP ? sssp_relax(status, p.epoch, v, du, __ldg(p.g.w + cur), stamp, ctl)
+                                          : bfs_claim(p.bitmap, status, v, level + 1);
+                    if (hit) {
+                        vb = __ldg(p.g.off + v);
+                        vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
+                        want = vd > 0;
+                    }
+                    ++cur;
+                }
+                wpush(wb, cnt, want, v, vb, vd);
+                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, osup);
+            }
+        }
+        __syncthreads();
+        const uint32_t nbig = s_nbig < (uint32_t)kBigCap ? s_nbig : (uint32_t)kBigCap;
+        for (uint32_t k = 0; k < nbig; ++k) {
+            const int64_t i = s_big[k];
+            const int64_t c0 = __ldg(in.beg + i);
+            const int64_t n0 = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
+            const uint32_t d0 = SSSP ? sssp_source_dist(status, p.epoch, __ldg(in.v + i), stamp) : 0u;
+            // warp w takes the 32-edge stripes w, w + 8, w + 16, ... of the node
+            serve_range<SSSP, ITEMS>(p, ctl, c0 + 32 * (int64_t)warp, c0 + n0, kBlock, d0, status, level, stamp, wb,
+                                     ws, cnt, osup);
+        }
     } else {
         const int64_t mdt = p.mdt;
         const int64_t stride = (int64_t)gridDim.x * kBlock;

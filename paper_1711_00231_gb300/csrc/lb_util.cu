@@ -63,7 +63,7 @@ __global__ void k_prepare(StepParams p, int32_t src, uint32_t *status, int kind,
     c->hp_from = kHpFromSuper;
     c->hp_sub = 0;
     c->sub_in = 0;
-    c->hp_kind = (p.hp_threshold > 0 && (int64_t)c->in_cnt < p.hp_threshold) ? 2u : 1u;
+    c->hp_kind = (p.hp_threshold > 0 && (int64_t)c->in_cnt < p.hp_threshold) ? 2u : (p.hp_mode == 1 ? 3u : 1u);
     c->blocks_done = 0;
     c->active = 1;
     c->error = 0;

@@ -37,7 +37,7 @@ class LbError(RuntimeError):
 class lb_options(ctypes.Structure):
     _fields_ = [("hist_bins", ctypes.c_int32), ("mdt_override", ctypes.c_int32), ("hp_threshold", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("wd_tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("hp_mode", ctypes.c_int32), ("hp_warp_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class lb_mem_stats(ctypes.Structure):

@@ -76,6 +76,34 @@ def test_rmat14_options():
         run_all(g, [0, 17], options=opts)
 
 
+@pytest.mark.parametrize("opts", [dict(hp_mode=1), dict(hp_mode=1, hp_threshold=-1),
+                                  dict(hp_mode=1, hp_threshold=-1, hp_warp_max=32),
+                                  dict(hp_mode=1, hp_threshold=-1, mdt_override=1)])
+def test_hp_degree_binned_matches_oracle(opts):
+    # HP's degree-binned form: every node of a list in one step, by its
+    # thread (<= min(MDT, 32) edges), its warp (<= hp_warp_max) or the whole CTA;
+    # hp_warp_max = 32 sends so many nodes to the CTA bin that its per-block
+    # list overflows onto the warps, mdt_override = 1 empties the thread bin
+    graphs = [(gg.rmat(14, 16, seed=1), [0, 17]), (gg.rmat(16, 16, seed=7), None),
+              (gg.grid(64, 48, seed=3), [0, 1000]), (gg.erdos_renyi(3000, 12000, seed=4), [5])]
+    for g, srcs in graphs:
+        if srcs is None:
+            srcs = [gg.max_degree_vertex(g)]
+        run_all(g, srcs, strategies=["HP"], options=opts)
+        G = lb.Graph.from_csr(g)
+        G.set_options(**opts)
+        try:
+            G.bfs(srcs[0], "HP")
+            modes = {int(r["mode"]) for r in G.trace()}
+            assert modes <= {2, 3}, modes   # lists under the threshold take the WD step
+            if opts.get("hp_threshold") == -1:
+                assert modes == {3}
+                # one binned step per level: no sub-iterations
+                assert len(G.trace()) == G.stats()["iterations"]
+        finally:
+            G.close()
+
+
 def test_grid_closed_form_and_oracle():
     R, C = 96, 80
     g = gg.grid(R, C, seed=1)
