@@ -59,6 +59,7 @@ def parse():
                     help="0: device-resident loop (CUDA graph WHILE); 1: host loop (for per-kernel profiling)")
     ap.add_argument("--kinds", default="bfs,sssp")
     ap.add_argument("--wd-tile", type=int, default=0, help="largest WD tile in list edges (0 = library default)")
+    ap.add_argument("--hp-mode", type=int, default=0, help="HP form: 0 sub-iterations, 1 degree-binned")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched-serving measurement")
     ap.add_argument("--serve-queries", type=int, default=1024)
     ap.add_argument("--serve-only", action="store_true", help="run only the batched-serving measurement")
@@ -491,6 +492,8 @@ def main():
         G.set_options(loop_mode=args.loop_mode)
     if args.wd_tile:
         G.set_options(wd_tile=args.wd_tile)
+    if args.hp_mode:
+        G.set_options(hp_mode=args.hp_mode)
     t_upload = time.time() - t0
     deg_t = torch.from_numpy(np.diff(g.offsets)).cuda()
     stream = torch.cuda.current_stream()
