@@ -104,6 +104,21 @@ def test_hp_degree_binned_matches_oracle(opts):
             G.close()
 
 
+def test_option_validation():
+    g = gg.rmat(10, 8, seed=1)
+    G = lb.Graph.from_csr(g)
+    try:
+        for bad in [dict(hp_mode=2), dict(hp_warp_max=16), dict(wd_tile=300), dict(wd_tile=65536), dict(loop_mode=3),
+                    dict(hist_bins=5000), dict(ctas_per_sm=40)]:
+            with pytest.raises(lb.LbError):
+                G.set_options(**bad)
+        G.set_options(hp_mode=1, hp_warp_max=64)
+        o = G.options()
+        assert o["hp_mode"] == 1 and o["hp_warp_max"] == 64
+    finally:
+        G.close()
+
+
 def test_grid_closed_form_and_oracle():
     R, C = 96, 80
     g = gg.grid(R, C, seed=1)
