@@ -221,7 +221,7 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out);
 lb_status lb_release_workspaces(lb_graph *g);
 
 /* Autotuner: times strategy s for `kind` from each of the nsrc sources
- * under a grid of options (WD tile size 512..4096, CTAs per SM, and for HP
+ * under a grid of options (WD tile size 1024..16384, CTAs per SM, and for HP
  * the WD-switch threshold), keeps the fastest on g and returns it in *best
  * with its mean query time in *best_ms (either may be NULL).  The other
  * option fields are kept as they were. */
