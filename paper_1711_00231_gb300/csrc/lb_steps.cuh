@@ -250,17 +250,19 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
 // the list recorded the entry holding every kTileGrain-th list edge, so tile
 // t starts in entry tstart[t * T / kTileGrain] (the paper's NodeOffset /
 // EdgeOffset, found without a scan or an offset kernel).  Each warp takes a
-// contiguous slice of T / 8 edges and walks it 32 edges per step, so
-// consecutive lanes read consecutive edges of a node (coalesced).  One binary search
-// per warp and tile finds the entry of the slice's first edge; after that
-// the warp keeps the current entry in registers and, per step, loads the
-// prefix and first edge of the next 32 entries (coalesced, L1).  An entry
-// starting inside the 32-edge window sets one bit of a mask (entries have
-// at least one edge, so at most 32 start in 32 positions); a lane's entry is
-// the current one plus the number of starts at or before its position, and
-// its prefix / first edge come from the loading lane by shuffle.  That
-// replaces a per-edge search (the bulk of the instructions) by a few
-// warp-wide operations per 32 edges.
+// contiguous slice of T / 8 edges and walks it, so consecutive lanes read
+// consecutive edges of a node (coalesced).  One warp-wide 32-way search per
+// warp and tile finds the entry of the slice's first edge; after that the
+// warp keeps the current entry in registers and a look-ahead window of the
+// next 32 entries' prefix and first edge (one per lane, reloaded only when
+// the walk advances).  Where the current entry reaches past the next 32
+// edges the warp runs through it with plain strided loads; elsewhere a
+// boundary step takes 32 edges: an entry starting inside the 32-edge window
+// sets one bit of a mask (entries have at least one edge, so at most 32
+// start in 32 positions); a lane's entry is the current one plus the number
+// of starts at or before its position, and its prefix / first edge come
+// from the loading lane by shuffle.  That replaces a per-edge search by a
+// few warp-wide operations per 32 edges.
 template <bool COH, class T>
 __device__ __forceinline__ T ld_list(const T *p) {
     return COH ? __ldcg(p) : __ldg(p);
