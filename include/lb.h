@@ -269,7 +269,12 @@ typedef struct lb_server_options {
     int32_t idle_us;      /* the kernel exits after this long with no work
                              (0 = 1000); it is relaunched on demand */
     double mem_fraction;  /* share of free HBM the slots may take (0 = 0.5) */
-    int32_t reserved[8];
+    int32_t launch_ms;    /* one persistent launch leaves after this long
+                             (0 = 600000, ten minutes); while queries are
+                             pending or in flight the next submit / poll
+                             relaunches it and they continue where they
+                             were (their state is in device memory) */
+    int32_t reserved[7];
 } lb_server_options;
 
 typedef struct lb_server_info_t {

@@ -531,6 +531,7 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
 #define PF_ADD(i, v)
 #endif
     if (threadIdx.x == 0) s_scan_from = blockIdx.x % (uint32_t)P.nslots;
+    const uint64_t t_launch = __ldcg(&P.sh->kernel_t0);  // written by k_serve_t0 before this launch
     for (;;) {
         // every thread has read the previous iteration's s_* values before
         // thread 0 overwrites them (without this barrier a lagging warp could
@@ -545,8 +546,15 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
             // slot's claim and job words, and the claimable slots are tried
             // in order until a claim holds
             const uint32_t lane = threadIdx.x;
+            // past the launch's time limit a CTA claims nothing more and
+            // leaves (checked before every claim: a CTA that keeps finding
+            // work, such as the one that opens a slot's next job, would
+            // otherwise never see the limit)
+            int late = 0;
+            if (lane == 0) late = global_ns() - t_launch > P.hard_ns;
+            late = __shfl_sync(kFull, late, 0);
             const uint32_t scan_from = s_scan_from;
-            const uint32_t nw = ((uint32_t)P.nslots + 31u) >> 5;
+            const uint32_t nw = late ? 0u : ((uint32_t)P.nslots + 31u) >> 5;
             const uint32_t sw = scan_from >> 5;
             int found = -1;
             uint32_t f_kind = 0, f_tiles = 0, f_tile = 0, f_q = 0;
@@ -605,7 +613,8 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
             if (lane == 0) {
                 if (found >= 0) s_scan_from = (uint32_t)found;
                 s_slot = found;
-                s_exit = 0;
+                s_exit = late;
+                if (late) atomicOr(&P.sh->error, kErrDeadline);
                 if (found >= 0) {
                     s_kind = f_kind;
                     s_tiles = f_tiles;
@@ -615,7 +624,7 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
             }
         }
         if (threadIdx.x == 0) {
-            if (s_slot < 0) {
+            if (s_slot < 0 && !s_exit) {
                 const uint64_t now = global_ns();
                 // Admission and the decision to stop are taken under one lock,
                 // so no request is admitted after the grid decided to leave.
@@ -634,12 +643,8 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
                     release_admit(P);
                 }
                 if (ld_acquire_sys32(&P.host->stop) != 0u || __ldcg(&P.sh->stopping) != 0u) s_exit = 1;
-                if (now - __ldcg(&P.sh->kernel_t0) > P.hard_ns) {
-                    atomicOr(&P.sh->error, kErrDeadline);
-                    s_exit = 1;
-                }
                 if (!s_exit) __nanosleep(256);
-            } else {
+            } else if (s_slot >= 0) {
                 idle_since = 0;
             }
         }
@@ -817,7 +822,7 @@ lb_status launch_kernel(lb_server *s) {
     P.tile_cap = s->tile_cap;
     P.slot_n = s->slot_n;
     P.idle_ns = (uint64_t)s->opt.idle_us * 1000ull;
-    P.hard_ns = 600ull * 1000000000ull;  // a persistent launch never outlives 10 minutes
+    P.hard_ns = (uint64_t)s->opt.launch_ms * 1000000ull;  // one persistent launch never outlives this
     k_serve_t0<<<1, 1, 0, s->stream>>>(s->d_shared);
     SV_CU(cudaGetLastError(), "k_serve_t0 launch");
     k_serve<<<s->grid, kBlock, 0, s->stream>>>(P);
@@ -837,7 +842,12 @@ lb_status ensure_running(lb_server *s) {
     // the kernel has left (idle timeout) while work is pending or in flight
     unsigned int err = 0;
     SV_CU(cudaMemcpy(&err, &s->d_shared->error, sizeof(err), cudaMemcpyDeviceToHost), "reading kernel status");
-    if (err & kErrDeadline) return sfail(LB_ERR_TIMEOUT, "persistent kernel reached its time limit");
+    if (err & kErrDeadline) {
+        // the launch reached its time limit with work left; every query's
+        // state (slots, jobs, claims) is in device memory and no CTA left in
+        // the middle of a tile, so a new launch continues them
+        SV_CU(cudaMemset(&s->d_shared->error, 0, sizeof(unsigned int)), "clearing kernel status");
+    }
     return launch_kernel(s);
 }
 
@@ -857,8 +867,9 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     if (o.tile == 0) o.tile = 8192;
     if (o.idle_us == 0) o.idle_us = 1000;
     if (o.mem_fraction <= 0.0) o.mem_fraction = 0.5;
+    if (o.launch_ms == 0) o.launch_ms = 600000;
     if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > kMaxSlots || o.idle_us < 0 ||
-        o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32) {
+        o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32 || o.launch_ms < 0) {
         delete s;
         return sfail(LB_ERR_ARG, "bad server options");
     }

@@ -160,6 +160,29 @@ def test_many_jobs_in_flight(mix):
         S.close()
 
 
+def test_queries_continue_across_launch_time_limits():
+    # a 2 ms launch limit: grid queries of thousands of iterations (tens of
+    # ms) outlive many launches, and each relaunch continues them from the
+    # state the slots keep in device memory; the results must still be exact
+    import torch
+    g = gg.grid(1024, 1024, seed=5)
+    G = lb.Graph.from_csr(g)
+    S = sv.Server([G], slots=4, launch_ms=2)
+    try:
+        reqs = [sv.Request(0.0, 0, 0, "sssp"), sv.Request(0.0, 0, g.n - 1, "sssp"), sv.Request(0.0, 0, 7, "bfs"),
+                sv.Request(0.0, 0, g.n // 2, "sssp")]
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in reqs]
+        st = S.run_batch(reqs, outs, timeout_s=120)
+        assert all(x == 0 for x in st), st
+        torch.cuda.synchronize()
+        for r, o in zip(reqs, outs):
+            assert np.array_equal(o.cpu().numpy(), reference(g, r.kind, r.src)), r
+        assert S.info()["kernel_launches"] >= 3
+    finally:
+        S.close()
+        G.close()
+
+
 def test_overflow_and_invalid_requests(mix):
     import torch
     graphs, handles = mix
