@@ -109,6 +109,21 @@ def test_argument_errors_need_no_gpu():
     assert L.lb_set_allocator(None, None, None) == lb.LB_OK
 
 
+def test_server_argument_errors_need_no_gpu():
+    L = lb.lib()
+    h = ctypes.c_void_p()
+    assert L.lb_server_create(None, 0, None, ctypes.byref(h)) == lb.LB_ERR_ARG
+    assert L.lb_server_create(None, 1, None, None) == lb.LB_ERR_ARG
+    tick = ctypes.c_uint64()
+    assert L.lb_server_submit(None, 0, 0, 0, None, ctypes.byref(tick)) == lb.LB_ERR_ARG
+    n = ctypes.c_int32()
+    assert L.lb_server_poll(None, None, 0, ctypes.byref(n)) == lb.LB_ERR_ARG
+    assert L.lb_server_state(None, None) == lb.LB_ERR_ARG
+    assert L.lb_server_info(None, None) == lb.LB_ERR_ARG
+    assert L.lb_server_stop(None) == lb.LB_ERR_ARG
+    assert L.lb_server_destroy(None) == lb.LB_OK
+
+
 def test_binding_names_match_header():
     for name in declared_functions():
         assert hasattr(lb, name), f"binding lacks {name}"
