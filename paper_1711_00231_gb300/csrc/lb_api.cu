@@ -222,14 +222,18 @@ void free_lists(lb_graph *g, NodeList *L, int64_t cap, int64_t tcap) {
     }
 }
 
+// On a failed allocation the lists allocated so far are released, so the
+// next attempt starts from nothing.
 lb_status alloc_lists(lb_graph *g, NodeList *L, int64_t cap, int64_t tcap, bool tiles) {
-    for (int b = 0; b < 2; ++b) {
-        LB_TRY(g->alloc(&L[b].v, cap));
-        LB_TRY(g->alloc(&L[b].beg, cap));
-        LB_TRY(g->alloc(&L[b].scan, cap + 1));
-        if (tiles) LB_TRY(g->alloc(&L[b].tstart, tcap));
+    lb_status st = LB_OK;
+    for (int b = 0; b < 2 && st == LB_OK; ++b) {
+        st = g->alloc(&L[b].v, cap);
+        if (st == LB_OK) st = g->alloc(&L[b].beg, cap);
+        if (st == LB_OK) st = g->alloc(&L[b].scan, cap + 1);
+        if (st == LB_OK && tiles) st = g->alloc(&L[b].tstart, tcap);
     }
-    return LB_OK;
+    if (st != LB_OK) free_lists(g, L, cap, tcap);
+    return st;
 }
 
 void free_workspace(lb_graph *g) {
@@ -292,10 +296,14 @@ int64_t node_list_cap(const lb_graph *g, int s) {
 // Allocates what strategy s needs; any reallocation invalidates the cached
 // device loops (their kernel parameters hold the pointers).
 lb_status ensure_workspace(lb_graph *g, int s) {
+    // each piece on its own, so an attempt after a failed allocation
+    // completes what the earlier one left
     if (!g->ctl) {
         LB_TRY(g->alloc(&g->ctl, 1));
         LB_CU(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream));
-        LB_TRY(g->alloc(&g->bitmap, (g->n + 31) / 32));
+    }
+    if (!g->bitmap) LB_TRY(g->alloc(&g->bitmap, (g->n + 31) / 32));
+    if (!g->epoch) {
         LB_TRY(g->alloc(&g->epoch, g->n));
         LB_CU(cudaMemsetAsync(g->epoch, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
     }
@@ -321,7 +329,7 @@ lb_status ensure_workspace(lb_graph *g, int s) {
             GraphDev gd{g->off, g->col, g->w, g->n, g->m};
             LB_CU(launch_coo_build(gd, g->coo_src, g->stream));
         }
-        if (g->elist_cap < g->m || !g->elist[0]) {
+        if (g->elist_cap < g->m || !g->elist[0] || !g->elist[1]) {
             quiesce(g);
             drop_execs(g);
             for (int b = 0; b < 2; ++b) g->release(g->elist[b], g->elist_cap);
@@ -353,6 +361,7 @@ lb_status ensure_workspace(lb_graph *g, int s) {
     if (s == LB_HP && !g->have_subs) {
         quiesce(g);
         drop_execs(g);
+        free_lists(g, g->subs, g->n, g->tile_cap);
         LB_TRY(alloc_lists(g, g->subs, g->n, g->tile_cap, true));
         g->have_subs = true;
     }

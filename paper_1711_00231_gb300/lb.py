@@ -101,7 +101,7 @@ class lb_step_record(ctypes.Structure):
 
 
 _lib = None
-_alloc_keepalive = None
+_alloc_keepalive = []  # every allocator callback pair ever installed
 
 
 def _load():
@@ -404,16 +404,16 @@ _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 def lb_set_allocator(alloc_fn=None, free_fn=None) -> None:
     """Install Python callables alloc(bytes) -> int and free(ptr) as the
-    library's device allocator (None, None restores cudaMalloc)."""
-    global _alloc_keepalive
+    library's device allocator (None, None restores cudaMalloc).  A graph
+    keeps the allocator it was created with, so every installed pair stays
+    alive for the life of the process."""
     if alloc_fn is None:
         _check(_load().lb_set_allocator(None, None, None))
-        _alloc_keepalive = None
         return
     a = _ALLOC_T(lambda size, ctx: alloc_fn(int(size)) or 0)
     f = _FREE_T(lambda ptr, ctx: free_fn(int(ptr)) if ptr else None)
     _check(_load().lb_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
-    _alloc_keepalive = (a, f)
+    _alloc_keepalive.append((a, f))
 
 
 def use_torch_allocator() -> None:

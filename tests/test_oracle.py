@@ -331,3 +331,13 @@ def test_generators_are_clean_and_deterministic():
     assert len(set(s.tolist())) == 16 and (g1.degrees()[s] > 0).all()
     er = gg.erdos_renyi(1000, 4000, seed=2)
     assert er.m <= 4000 and er.m > 3900
+
+
+def test_rmat_split_fraction_is_small():
+    # Sec. III-B reports that fewer than 5% of the nodes undergo splitting at
+    # the histogram MDT on its skewed graphs; the R-MAT stand-ins agree
+    for scale in (14, 20):
+        g = gg.rmat(scale, 16, seed=1)
+        mdt = oracle.mdt(g.offsets, 10)[0]
+        deg = np.diff(g.offsets)
+        assert (deg > mdt).sum() / g.n < 0.05, scale
