@@ -11,12 +11,14 @@
 // queries interleave freely on the GPU and no grid-wide barrier exists.
 //
 // Requests arrive through a ring in pinned, device-mapped host memory: the
-// host writes a request and then bumps `submitted`; an idle CTA that wins
-// the admission lock moves pending requests into free slots.  Completions
-// go back through a second mapped ring (one record per query, published by
-// a sequence number written last).  The kernel leaves when it has had
-// nothing to do for idle_ns, when the host raises `stop`, or at a hard time
-// limit; the host relaunches it when work is pending and it has exited.
+// host writes a request and then bumps `submitted`; a CTA that wins the
+// admission lock (CTAs without work on every pass, busy ones now and then)
+// moves pending requests into free slots.  Completions go back through a
+// second mapped ring (one record per query, published by a sequence number
+// written last).  The kernel leaves when it has had nothing to do for
+// idle_ns, when the host raises `stop`, or once its launch time limit has
+// passed (no CTA claims a tile after it); the host relaunches it while work
+// is pending or in flight, and the queries continue from the slots' state.
 //
 // All loads of data other CTAs write during the kernel (worklists, status,
 // bitmap, stamps) bypass L1 (ld.global.cg), because L1 is not coherent
