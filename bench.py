@@ -610,12 +610,19 @@ def main():
         cmp_src = srcs[:args.compare_sources]
         for kind in kinds:
             row = {}
-            for label in ("BS", "EP", "WD", "NS", "HP", "HP_binned"):
+            # every strategy's result is compared with WD's, element by element
+            # (WD itself equals the oracle in the GPU tests on this workload)
+            wd_ref = {}
+            for s in cmp_src:
+                query(kind, s, "WD")
+                wd_ref[int(s)] = out.clone()
+            for label in ("BS", "EP", "WD", "NS", "HP", "HP_binned", "NS_PHYS"):
                 # HP_binned: HP with hp_mode 1 (degree-binned sub-worklists in one step)
                 s_name = "HP" if label == "HP_binned" else label
                 G.set_options(hp_mode=1 if label == "HP_binned" else 0)
                 tot = 0.0
                 e_tot = 0
+                exact = True
                 for s in cmp_src:
                     query(kind, s, s_name)   # warm (builds its workspace / loop)
                     torch.cuda.synchronize()
@@ -626,8 +633,10 @@ def main():
                     torch.cuda.synchronize()
                     tot += a.elapsed_time(b)
                     e_tot += work[(kind, int(s))][0]
-                    assert G.stats()["status"] == 0
-                row[label] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9}
+                    exact = exact and G.stats()["status"] == 0 and bool(torch.equal(out, wd_ref[int(s)]))
+                row[label] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9,
+                              "exact_vs_wd": exact}
+            del wd_ref
             G.set_options(hp_mode=0)
             row["speedup_wd_vs_bs"] = row["BS"]["ms_per_query"] / row["WD"]["ms_per_query"]
             row["speedup_wd_vs_ep"] = row["EP"]["ms_per_query"] / row["WD"]["ms_per_query"]

@@ -350,10 +350,13 @@ lb_status lb_server_stop(lb_server *s);
  *
  * offsets_dev (n+1 int64), cols_dev (m int32) and levels_dev (n int32,
  * receives hop counts, -1 unreachable) are caller-owned device pointers on
- * the current device; no lb_graph is used and the CSR is not validated.
- * All other memory comes from one fixed array of device memory inside the
- * library (about 3.6 MiB; every GPU that loads the library holds it until
- * the process exits), so the call allocates nothing.  Limits: n <= 131072
+ * the current device; no lb_graph is used.  The CSR is checked on the
+ * device before the traversal (offsets[0] = 0, non-decreasing, offsets[n] =
+ * m, every column in [0, n)); a malformed one returns LB_ERR_ARG and
+ * nothing else runs.  All other memory comes from one fixed array of device
+ * memory inside the library (about 3.6 MiB; every GPU that loads the
+ * library holds it until the process exits), so the call allocates
+ * nothing.  Limits: n <= 131072
  * and m <= 16777216; larger sizes return LB_ERR_ARG.  The first call on a
  * device looks the array up (cudaGetSymbolAddress) and should come before
  * any stream capture.  Every call shares the array; calls whose GPU work

@@ -867,8 +867,16 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
         if (!g->out_internal) LB_TRY(g->alloc(&g->out_internal, g->n));
         out = g->out_internal;
     }
+    // any failure part way through puts the caller's options back
+    auto restore = [&](lb_status st) {
+        const std::string msg = t_err;
+        lb_set_options(g, &base);
+        t_err = msg;
+        return st;
+    };
     for (const lb_options &o : cands) {
-        LB_TRY(lb_set_options(g, &o));
+        lb_status so = lb_set_options(g, &o);
+        if (so != LB_OK) return restore(so);
         double tot = 0.0;
         bool ok = true;
         for (int32_t i = 0; i < nsrc && ok; ++i) {
@@ -879,9 +887,10 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
                     DeviceGuard dg(g->device);
                     st = run_query(g, kind, s, srcs[i], out, nullptr, g->stream);
                 }
-                if (st != LB_OK) return st;
+                if (st != LB_OK) return restore(st);
                 lb_query_stats qs;
-                LB_TRY(lb_last_stats(g, &qs));
+                st = lb_last_stats(g, &qs);
+                if (st != LB_OK) return restore(st);
                 if (qs.status != LB_OK && qs.status != LB_ERR_OVERFLOW) ok = false;
                 if (rep == 1) tot += qs.device_ms;
             }

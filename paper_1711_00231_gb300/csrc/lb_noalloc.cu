@@ -13,7 +13,10 @@
 // Limits: n <= 131072 vertices and m <= 16777216 edges (about 3.6 MiB of
 // scratch).  Every call on a device shares the array and finds the previous
 // call's contents in it; the kernels reset what must start at zero (loop
-// counters, the visited bitmap and the output levels).  Calls whose work
+// counters, the visited bitmap, the validation word and the output levels).
+// The caller's CSR is checked on the device before any traversal (offsets
+// start at 0, never decrease and end at m; every column is in [0, n)), so a
+// malformed graph is refused instead of indexing outside the array.  Calls whose work
 // overlaps on the GPU (different streams without ordering, or threads
 // calling concurrently) race on the array and give wrong results.
 #include <cstdio>
@@ -42,7 +45,8 @@ constexpr size_t kListBeg = align256(sizeof(int32_t) * (size_t)kNaMaxN);
 constexpr size_t kListScan = align256(sizeof(int32_t) * (size_t)(kNaMaxN + 1));
 constexpr size_t kListTiles = align256(sizeof(int32_t) * (size_t)kNaTiles);
 constexpr size_t kListBytes = kListV + kListBeg + kListScan + kListTiles;
-constexpr size_t kOffLists = align256(kOffEpoch + sizeof(uint32_t));  // BFS needs no stamps
+constexpr size_t kOffValid = align256(kOffEpoch + sizeof(uint32_t));  // one stamp word: BFS needs no stamps
+constexpr size_t kOffLists = align256(kOffValid + sizeof(uint32_t));
 constexpr size_t kNaBytes = kOffLists + 2 * kListBytes;
 
 static __device__ __align__(256) unsigned char lb_noalloc_scratch[kNaBytes];
@@ -117,6 +121,16 @@ extern "C" lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t
     p.use_cond = 0;
     const int grid = step_blocks_per_sm(LB_WD, false) * sms;
     cudaStream_t st = (cudaStream_t)stream;
+    // the caller's CSR shape, checked before the traversal indexes with it
+    uint32_t *verr = (uint32_t *)(base + kOffValid);
+    uint32_t vword = 0;
+    e = cudaMemsetAsync(verr, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = launch_validate(p.g, verr, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&vword, verr, sizeof(vword), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return na_fail(LB_ERR_CUDA, "CSR validation", e);
+    if (vword & kErrShape)
+        return na_fail(LB_ERR_ARG, "malformed CSR (offsets not 0..m and non-decreasing, or a column outside [0, n))");
     const uint32_t max_levels = (uint32_t)(n + 1);
     e = launch_prepare(p, src, (uint32_t *)levels_dev, LB_KIND_BFS, max_levels, (uint64_t)1 << 40,
                        (uint64_t)60 * 1000000000ull, st);

@@ -201,24 +201,73 @@ def test_erdos_renyi_er20_shape():
         G.close()
 
 
-def test_grid4096_sssp_from_corner():
-    # 4096 x 4096 grid, weights U[1,1000], source at the corner
-    g = gg.grid(4096, 4096, seed=1)
+# every strategy and form, as (strategy, options) pairs: the paper's HP
+# sub-iterations and the degree-binned HP step are both run
+ALL_FORMS = [(s, dict(hp_mode=0)) for s in STRATS] + [("HP", dict(hp_mode=1))]
+
+
+def run_forms(G, g, src, ref_lev, ref_dist, forms=ALL_FORMS):
+    """Every form's BFS levels and SSSP distances from src, compared with
+    the oracle's element by element."""
+    for s, opts in forms:
+        G.set_options(**opts)
+        lev = G.bfs(src, s)
+        assert G.stats()["status"] == 0, (s, opts)
+        assert np.array_equal(lev, ref_lev), f"BFS {s} {opts} src={src}: {np.flatnonzero(lev != ref_lev)[:10]}"
+        if ref_dist is not None:
+            d, rc = G.sssp(src, s)
+            assert rc == lb.LB_OK, (s, opts, rc)
+            assert np.array_equal(d, ref_dist), f"SSSP {s} {opts} src={src}: {np.flatnonzero(d != ref_dist)[:10]}"
+    G.set_options(hp_mode=0)
+
+
+@pytest.fixture(scope="module")
+def grid4096():
+    # 4096 x 4096 grid, 4-neighbour, weights U[1,1000], seed 1
+    return gg.grid(4096, 4096, seed=1)
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    # R-MAT scale 24, edge factor 32, a/b/c/d = .57/.19/.19/.05, weights
+    # U[1,255], seed 1 (the benchmark's graph)
+    return gg.rmat(24, 32, seed=1)
+
+
+def test_grid4096_sssp_from_corner(grid4096):
+    # the high-diameter configuration, every strategy and form: SSSP from the
+    # corner against Dijkstra, BFS against the oracle and the closed form
+    # r + c (8,191 levels)
+    g = grid4096
     ref, _ = oracle.dijkstra(g, 0)
+    ref_lev, _ = oracle.bfs(g, 0)
+    r, c = np.divmod(np.arange(g.n), 4096)
+    assert np.array_equal(ref_lev, (r + c).astype(np.int32))
     G = lb.Graph.from_csr(g)
     try:
-        for s in ["WD", "BS", "HP"]:
-            d, rc = G.sssp(0, s)
-            assert rc == lb.LB_OK and np.array_equal(d, ref), s
-        lev = G.bfs(0, "WD")
-        r, c = np.divmod(np.arange(g.n), 4096)
-        assert np.array_equal(lev, (r + c).astype(np.int32))
+        run_forms(G, g, 0, ref_lev, ref)
+        G.bfs(0, "WD")
         assert G.stats()["iterations"] == 8191
     finally:
         G.close()
 
 
-def test_rmat24_bench_workload():
+def test_rmat24_every_strategy(rmat24):
+    # the benchmark's graph: every strategy and form from the first of its
+    # 64 sources, BFS levels and SSSP distances against the oracle in full
+    g = rmat24
+    src = int(gg.pick_sources(g, 64, seed=1)[0])
+    ref_lev, _ = oracle.bfs(g, src)
+    ref, ov = oracle.dijkstra(g, src)
+    assert not ov
+    G = lb.Graph.from_csr(g)
+    try:
+        run_forms(G, g, src, ref_lev, ref)
+    finally:
+        G.close()
+
+
+def test_rmat24_bench_workload(rmat24):
     # the bench's workload and launch configuration: R-MAT scale 24, edge
     # factor 32, weights U[1,255], two of its 64 sources (seed 1), WD through
     # the device loop.  BFS levels are compared with the oracle's BFS in
@@ -227,7 +276,7 @@ def test_rmat24_bench_workload():
     # a tight in-edge), which holds only for the exact distances, and the
     # first source's distances are also compared with Dijkstra in full.
     import torch
-    g = gg.rmat(24, 32, seed=1)
+    g = rmat24
     srcs = gg.pick_sources(g, 64, seed=1)[:2].tolist()
     G = lb.Graph.from_csr(g)
     try:

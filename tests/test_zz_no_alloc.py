@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 from paper_1711_00231_gb300 import lb
 
 pytestmark = pytest.mark.gpu
@@ -50,3 +51,48 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(lb.LbError) as ei:
         lb.lb_bfs_wd_noalloc(off, off, 3, (1 << 24) + 1, 0, lev)
     assert ei.value.status == lb.LB_ERR_ARG
+
+
+def test_noalloc_at_the_size_limit_then_a_smaller_graph():
+    # n = 131,072 exactly (the array's vertex limit): the upper half of the
+    # bitmap, both list buffers and the tile-start region are in use.  A
+    # smaller graph right after it finds that call's leftovers in the array
+    # (stale list entries, bitmap words past its own n) and must still be
+    # exact.
+    import torch
+    big = gg.rmat(17, 16, seed=3, weights=None)
+    small = gg.rmat(11, 8, seed=4, weights=None)
+    assert big.n == 1 << 17
+    for g, src in ((big, gg.max_degree_vertex(big)), (small, 0), (small, gg.max_degree_vertex(small))):
+        off = torch.from_numpy(g.offsets).cuda()
+        col = torch.from_numpy(g.cols).cuda()
+        out = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+        lb.lb_bfs_wd_noalloc(off, col, g.n, g.m, src, out, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), oracle.bfs(g, src)[0]), (g.n, src)
+
+
+def test_noalloc_refuses_a_malformed_csr():
+    # the caller's CSR is checked on the device before the traversal: a
+    # column equal to n, or offsets that do not end at m, return LB_ERR_ARG
+    # and leave the output untouched
+    import torch
+    g = gg.rmat(10, 8, seed=6, weights=None)
+    off = torch.from_numpy(g.offsets).cuda()
+    bad_col = g.cols.copy()
+    bad_col[g.m // 2] = g.n
+    bad_off = g.offsets.copy()
+    bad_off[-1] = g.m - 1
+    for o, c in ((off, torch.from_numpy(bad_col).cuda()),
+                 (torch.from_numpy(bad_off).cuda(), torch.from_numpy(g.cols).cuda())):
+        out = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+        with pytest.raises(lb.LbError) as ei:
+            lb.lb_bfs_wd_noalloc(o, c, g.n, g.m, 0, out, torch.cuda.current_stream())
+        assert ei.value.status == lb.LB_ERR_ARG and "malformed" in str(ei.value)
+        torch.cuda.synchronize()
+        assert bool((out == 7).all())
+    # a well-formed call afterwards is unaffected
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    lb.lb_bfs_wd_noalloc(off, torch.from_numpy(g.cols).cuda(), g.n, g.m, 0, out, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.bfs(g, 0)[0])
