@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--kinds", default="bfs,sssp")
     ap.add_argument("--wd-tile", type=int, default=0, help="largest WD tile in list edges (0 = library default)")
     ap.add_argument("--hp-mode", type=int, default=0, help="HP form: 0 sub-iterations, 1 degree-binned")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default options)")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched-serving measurement")
     ap.add_argument("--serve-queries", type=int, default=1024)
     ap.add_argument("--serve-only", action="store_true", help="run only the batched-serving measurement")
@@ -253,16 +254,21 @@ def run_reference(args):
 
 
 def small_configs(torch, reps: int = 3):
-    """The two smaller R-MAT configurations, every strategy: scale 14 (edge
-    factor 16, BFS from vertex 0) and scale 20 (edge factor 16, weights
-    U[1,255], BFS and SSSP from the highest-degree vertex).  ms per query
-    (mean of `reps` warm runs, CUDA events) and GTEPS = m_reached / time."""
+    """The two smaller R-MAT configurations and the ER23 shape, every
+    strategy: R-MAT scale 14 (edge factor 16, BFS from vertex 0), R-MAT scale
+    20 (edge factor 16, weights U[1,255], BFS and SSSP from the
+    highest-degree vertex) and Erdos-Renyi with 2^23 vertices and 33.55M
+    edges (Table II's ER23 shape; BFS and SSSP from a seeded source).  ms per
+    query (mean of `reps` warm runs, CUDA events) and GTEPS = m_reached /
+    time."""
     import graphgen as gg
     from paper_1711_00231_gb300 import lb
     out = {}
     g20 = gg.rmat(20, 16, seed=1)
+    er23 = gg.erdos_renyi(1 << 23, 33554432, seed=1)
     for name, g, src, kinds in (("rmat14_ef16_vertex0", gg.rmat(14, 16, seed=1), 0, ("bfs",)),
-                                ("rmat20_ef16_maxdeg", g20, gg.max_degree_vertex(g20), ("bfs", "sssp"))):
+                                ("rmat20_ef16_maxdeg", g20, gg.max_degree_vertex(g20), ("bfs", "sssp")),
+                                ("er23_33m_uniform", er23, int(gg.pick_sources(er23, 1, seed=1)[0]), ("bfs", "sssp"))):
         G = lb.Graph.from_csr(g)
         buf = torch.empty(g.n, dtype=torch.int32, device="cuda")
         deg = np.diff(g.offsets)
@@ -495,12 +501,23 @@ def main():
     if args.hp_mode:
         G.set_options(hp_mode=args.hp_mode)
     t_upload = time.time() - t0
+    kinds = tuple(k for k in args.kinds.split(",") if k)
+    strat = args.strategy
+    # the library's autotuner picks the options (tile size, CTAs per SM,
+    # bin thresholds, granule size, ... for the strategy) on two sources of
+    # a separate draw; the timed queries run with what it chose
+    tune = None
+    if not args.no_tune and not args.wd_tile:
+        t0 = time.time()
+        tsrc = gg.pick_sources(g, 2, seed=2)
+        best, best_ms = G.autotune("both" if len(kinds) == 2 else kinds[0], strat, tsrc)
+        tune = {"options": best, "ms_per_source": best_ms, "sources": [int(s) for s in tsrc],
+                "seconds": time.time() - t0}
+    run_opts = G.options()
     deg_t = torch.from_numpy(np.diff(g.offsets)).cuda()
     stream = torch.cuda.current_stream()
     n = g.n
     out = torch.empty(n, dtype=torch.int32, device="cuda")
-    kinds = tuple(k for k in args.kinds.split(",") if k)
-    strat = args.strategy
 
     def query(kind, s, strategy=strat):
         if kind == "bfs":
@@ -685,7 +702,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "uint32", "data": "synthetic",
                 "config": dict(WORKLOAD, strategy=strat, parallelism=f"replicas{world}", n=g.n, m=g.m,
                                scale=args.scale, edge_factor=args.edge_factor, sources=len(srcs), kinds=list(kinds),
-                               loop="device (CUDA graph WHILE)" if args.loop_mode == 0 else "host"),
+                               loop="device (CUDA graph WHILE)" if args.loop_mode == 0 else "host",
+                               options=run_opts, autotune=tune),
                 "roofline": roofline, "roofline_by_kind": roofline_by_kind, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
                 "gpu_launches": sum(res[k]["launches"] for k in kinds),

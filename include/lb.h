@@ -99,11 +99,28 @@ typedef struct lb_options {
                               sub-list); 1 = one step per super-iteration
                               with the list's nodes binned by degree into
                               sub-worklists served by a thread (<= min(MDT,
-                              32) edges), a warp (<= hp_warp_max) or the
-                              whole CTA (more) (0) */
-    int32_t hp_warp_max;   /* hp_mode 1: largest degree a warp serves; larger
-                              nodes go to the CTA bin (4096) */
-    int32_t reserved[8];
+                              thread_max) edges), a warp (<= hp_warp_max) or
+                              the whole CTA (more) (0) */
+    int32_t hp_warp_max;   /* binned forms (hp_mode 1, ns_mode 1): largest
+                              entry a warp serves; larger entries go to the
+                              CTA bin (4096) */
+    int32_t ns_mode;       /* NS form: 0 = the paper's thread per granule
+                              (Sec. III-B: a split node's ceil(d/MDT) runs of
+                              at most MDT edges, one thread each); 1 = the
+                              same granules served by a thread (<=
+                              thread_max edges), a warp (<= hp_warp_max) or
+                              the whole CTA (0) */
+    int32_t thread_max;    /* binned forms: largest entry one thread serves,
+                              1..1024 (32) */
+    int32_t hp_depth;      /* HP hierarchy depth, 1..8 (1): the first
+                              hp_depth lists of a super-iteration's chain
+                              (the super list, its sub-list, ...) each get
+                              their own MDT, the histogram MDT of the
+                              remaining degrees of that list's entries (the
+                              super list uses the graph's MDT); later
+                              sub-lists keep the last one (Sec. III-C: "the
+                              depth of this hierarchy is tunable") */
+    int32_t reserved[5];
 } lb_options;
 
 /* Device bytes by structure (lb_mem_report).  "extra" is everything a
@@ -113,7 +130,10 @@ typedef struct lb_mem_stats {
     int64_t csr_cols;      /* 4 m */
     int64_t csr_weights;   /* 4 m, 0 for an unweighted graph */
     int64_t status;        /* level / dist working array, 4 n */
-    int64_t visited;       /* BFS visited bitmap + SSSP per-iteration stamps */
+    int64_t visited;       /* two bitmaps of n bits (each rounded up to 16
+                              bytes): BFS visited bits in the first; SSSP
+                              "queued in this iteration" bits of even and
+                              odd iterations in both */
     int64_t node_lists;    /* node worklists (two buffers: id, first edge,
                               edge prefix) */
     int64_t tile_starts;   /* WD/HP: worklist entry holding every 256th
@@ -220,11 +240,19 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out);
 /* Releases every query workspace of g (the CSR stays). */
 lb_status lb_release_workspaces(lb_graph *g);
 
-/* Autotuner: times strategy s for `kind` from each of the nsrc sources
- * under a grid of options (WD tile size 1024..16384, CTAs per SM, and for HP
- * the WD-switch threshold), keeps the fastest on g and returns it in *best
- * with its mean query time in *best_ms (either may be NULL).  The other
- * option fields are kept as they were. */
+/* Autotuner: times strategy s from each of the nsrc sources (kind
+ * LB_KIND_BFS, LB_KIND_SSSP, or 2 for one BFS and one SSSP per source) under
+ * a grid of options, keeps the fastest on g and returns it in *best with its
+ * mean time per source in *best_ms (either may be NULL).  The grid per
+ * strategy: WD -- the largest tile (2048..16384 edges) x CTAs per SM (the
+ * occupancy limit, 2, 3, 4); HP -- the paper's sub-iterations with switch
+ * threshold 256 / 1024 / 4096 x hierarchy depth 1..3, and the binned form
+ * with threshold 256 / 1024 x thread bin 8 / 32 / 128 x warp bin 512 /
+ * 4096 edges; NS -- the granule size (MDT from the histogram, or 32 / 256 /
+ * 2048) in the paper's form, and the binned form with the histogram MDT or
+ * 256 / 2048 x thread bin 8 / 32 / 128; NS_PHYS -- the granule size; BS, EP
+ * -- CTAs per SM.  Fields outside the grid keep their values.  On any
+ * failure the options in force before the call are restored. */
 lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *srcs, int32_t nsrc, lb_options *best,
                       double *best_ms);
 

@@ -52,7 +52,7 @@ def _load():
             "oracle_wd_offsets": ([i64, P, i64, P, P], i64),
             "oracle_ns_chunks": ([i64, i64, P, i64], i64),
             "oracle_ns_split": ([i64, P, i64, P], i64),
-            "oracle_hp_schedule": ([i64, P, i64, i64, P, P, P, i64], i64),
+            "oracle_hp_schedule": ([i64, P, i64, i64, i32, i32, P, P, P, i64], i64),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -178,14 +178,17 @@ def ns_split(offsets, mdt_: int):
     return int(ch), int(ns.value)
 
 
-def hp_schedule(deg, mdt_: int, threshold: int, cap: int = 1 << 16):
+def hp_schedule(deg, mdt_: int, threshold: int, cap: int = 1 << 16, depth: int = 1, bins: int = 10):
     """Steps of hierarchical processing over one super worklist: arrays of
-    (list size, edges relaxed, mode 0 = sub-iteration / 1 = WD)."""
+    (list size, edges relaxed, mode 0 = sub-iteration / 1 = WD).  depth > 1:
+    the first `depth` lists of the chain each take their own MDT (the
+    histogram rule over the sub-list's remaining degrees, `bins` bins); the
+    super list uses mdt_."""
     d = np.ascontiguousarray(deg, dtype=np.int64)
     ls = np.empty(cap, dtype=np.int64)
     ed = np.empty(cap, dtype=np.int64)
     md = np.empty(cap, dtype=np.int32)
-    k = _load().oracle_hp_schedule(d.size, _p(d), mdt_, threshold, _p(ls), _p(ed), _p(md), cap)
+    k = _load().oracle_hp_schedule(d.size, _p(d), mdt_, threshold, depth, bins, _p(ls), _p(ed), _p(md), cap)
     if k < 0:
         raise ValueError("oracle_hp_schedule: bad arguments")
     k = min(int(k), cap)

@@ -388,15 +388,46 @@ int64_t oracle_ns_split(int64_t n, const int64_t *off, int64_t mdt, int64_t *n_s
  * relax its next min(mdt, remaining) edges, i.e. edges s*mdt .. s*mdt+mdt-1
  * of its list; nodes with edges left form the next list.  The iteration ends
  * when the list is empty.  For each step k (at most cap) the function writes
- * the list size, the edges relaxed and the mode; it returns the step count. */
-int64_t oracle_hp_schedule(int64_t F, const int64_t *deg, int64_t mdt, int64_t threshold, int64_t *list_size,
-                           int64_t *edges, int32_t *mode, int64_t cap) {
-    if (mdt < 1 || F < 0) return -1;
+ * the list size, the edges relaxed and the mode; it returns the step count.
+ *
+ * Hierarchy depth (Sec. III-C: a large sub-worklist "can be further
+ * partitioned", the depth is tunable and the histogram MDT decides the
+ * split).  Read here as: the lists of one super-iteration form a chain (the
+ * super list, its sub-list, that list's sub-list, ...); each of the first
+ * `depth` lists takes its own MDT -- the super list the given mdt (the
+ * graph's histogram MDT), a sub-list the histogram rule applied to its
+ * nodes' remaining degrees with `bins` bins -- and later lists keep the last
+ * one.  depth = 1 is the single-MDT schedule of the HP algorithm. */
+/* The histogram MDT rule of Sec. III-B over an array of degrees (the
+ * remaining degrees of a sub-list): bins of equal width over (0, max], the
+ * tallest bin k (1-based, smallest on a tie), MDT = max(1, floor(k max /
+ * bins)); 0 when every degree is 0. */
+static int64_t mdt_of_degrees(int64_t F, const int64_t *d, int32_t bins) {
+    int64_t maxdeg = 0;
+    for (int64_t i = 0; i < F; ++i)
+        if (d[i] > maxdeg) maxdeg = d[i];
+    if (maxdeg == 0) return 0;
+    int64_t *hist = (int64_t *)calloc((size_t)bins + 1, sizeof(int64_t));
+    if (!hist) return -1;
+    for (int64_t i = 0; i < F; ++i)
+        if (d[i] > 0) hist[(d[i] * (int64_t)bins + maxdeg - 1) / maxdeg]++;
+    int32_t best = 1;
+    for (int32_t k = 2; k <= bins; ++k)
+        if (hist[k] > hist[best]) best = k;
+    free(hist);
+    int64_t mdt = ((int64_t)best * maxdeg) / bins;
+    return mdt < 1 ? 1 : mdt;
+}
+
+int64_t oracle_hp_schedule(int64_t F, const int64_t *deg, int64_t mdt, int64_t threshold, int32_t depth, int32_t bins,
+                           int64_t *list_size, int64_t *edges, int32_t *mode, int64_t cap) {
+    if (mdt < 1 || F < 0 || depth < 1 || bins < 1) return -1;
     int64_t *rem = (int64_t *)malloc((size_t)(F > 0 ? F : 1) * sizeof(int64_t));
     if (!rem) return -1;
     int64_t live = F;
     for (int64_t i = 0; i < F; ++i) rem[i] = deg[i];
     int64_t steps = 0;
+    int64_t cur = mdt; /* edges per node in this sub-iteration */
     while (live > 0) {
         int64_t relaxed = 0;
         int32_t md;
@@ -404,8 +435,15 @@ int64_t oracle_hp_schedule(int64_t F, const int64_t *deg, int64_t mdt, int64_t t
             for (int64_t i = 0; i < F; ++i) { relaxed += rem[i]; rem[i] = 0; }
             md = 1;
         } else {
+            /* list number `steps` of the chain (0 = the super list, which
+             * keeps the graph's MDT): within the first `depth` lists a
+             * sub-list takes the MDT of its own remaining degrees */
+            if (steps > 0 && steps < depth) {
+                cur = mdt_of_degrees(F, rem, bins);
+                if (cur < 1) { free(rem); return -1; }
+            }
             for (int64_t i = 0; i < F; ++i) {
-                int64_t take = rem[i] < mdt ? rem[i] : mdt;
+                int64_t take = rem[i] < cur ? rem[i] : cur;
                 relaxed += take;
                 rem[i] -= take;
             }

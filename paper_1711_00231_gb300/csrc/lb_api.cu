@@ -79,10 +79,16 @@ struct DeviceGuard {
 
 constexpr int kStrategies = 7;
 
+constexpr int32_t LB_TUNE_BOTH = 2;  // lb_autotune: time a BFS and an SSSP per source
+
 bool is_ep(int s) { return s == LB_EP || s == LB_EP_NOCHUNK; }
 
 // tile-start entries a list needs: one per kTileGrain worklist edges
 int64_t round_tiles(int64_t m) { return m / kTileGrain + 2; }
+
+// words of one half of the visited / queued bitmap: one bit per vertex,
+// rounded up to whole 16-byte groups
+int64_t bitmap_words(int64_t n) { return ((n + 31) / 32 + 3) / 4 * 4; }
 
 }  // namespace
 
@@ -105,8 +111,7 @@ struct lb_graph {
 
     // workspace (lazily allocated)
     Ctl *ctl = nullptr;
-    uint32_t *bitmap = nullptr;
-    uint32_t *epoch = nullptr;
+    uint32_t *bitmap = nullptr;  // 2 * bitmap_words(n): BFS visited bits / SSSP queued bits
     uint32_t *out_internal = nullptr;  // result buffer of host-output queries
     int32_t *par_internal = nullptr;
     NodeList lists[2]{};
@@ -174,6 +179,9 @@ lb_options default_options() {
     o.hp_threshold = 1024;
     o.hp_mode = 0;
     o.hp_warp_max = 4096;
+    o.ns_mode = 0;
+    o.thread_max = 32;
+    o.hp_depth = 1;
     o.loop_mode = 0;
     o.wd_tile = 8192;
     o.ctas_per_sm = 0;
@@ -188,6 +196,13 @@ lb_status normalise_options(const lb_options *in, lb_options *out) {
     if (o.hp_warp_max == 0) o.hp_warp_max = d.hp_warp_max;
     if (o.hp_mode != 0 && o.hp_mode != 1) return fail(LB_ERR_ARG, "hp_mode must be 0 or 1");
     if (o.hp_warp_max < 32) return fail(LB_ERR_ARG, "hp_warp_max must be >= 32");
+    if (o.thread_max == 0) o.thread_max = d.thread_max;
+    if (o.hp_depth == 0) o.hp_depth = d.hp_depth;
+    if (o.ns_mode != 0 && o.ns_mode != 1) return fail(LB_ERR_ARG, "ns_mode must be 0 or 1");
+    if (o.thread_max < 1 || o.thread_max > 1024) return fail(LB_ERR_ARG, "thread_max must be in [1, 1024]");
+    if (o.hp_depth < 1 || o.hp_depth > 8) return fail(LB_ERR_ARG, "hp_depth must be in [1, 8]");
+    for (int i = 0; i < 5; ++i)
+        if (o.reserved[i] != 0) return fail(LB_ERR_ARG, "reserved option fields must be 0");
     if (o.wd_tile == 0) o.wd_tile = d.wd_tile;
     if (o.hist_bins < 1 || o.hist_bins > 4096) return fail(LB_ERR_ARG, "hist_bins must be in [1, 4096]");
     if (o.mdt_override < 0) return fail(LB_ERR_ARG, "mdt_override must be >= 0");
@@ -239,8 +254,7 @@ lb_status alloc_lists(lb_graph *g, NodeList *L, int64_t cap, int64_t tcap, bool 
 void free_workspace(lb_graph *g) {
     drop_execs(g);
     g->release(g->ctl, 1);
-    g->release(g->bitmap, (g->n + 31) / 32);
-    g->release(g->epoch, g->n);
+    g->release(g->bitmap, 2 * bitmap_words(g->n));
     g->release(g->out_internal, g->n);
     g->release(g->par_internal, g->n);
     free_lists(g, g->lists, g->list_cap, g->tile_cap);
@@ -302,11 +316,7 @@ lb_status ensure_workspace(lb_graph *g, int s) {
         LB_TRY(g->alloc(&g->ctl, 1));
         LB_CU(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), g->stream));
     }
-    if (!g->bitmap) LB_TRY(g->alloc(&g->bitmap, (g->n + 31) / 32));
-    if (!g->epoch) {
-        LB_TRY(g->alloc(&g->epoch, g->n));
-        LB_CU(cudaMemsetAsync(g->epoch, 0, sizeof(uint32_t) * (size_t)g->n, g->stream));
-    }
+    if (!g->bitmap) LB_TRY(g->alloc(&g->bitmap, 2 * bitmap_words(g->n)));
     if (s == LB_NS || s == LB_NS_PHYS || s == LB_HP) LB_TRY(ensure_mdt(g));
     if (s == LB_NS_PHYS && g->phys_mdt != g->mdt) {
         quiesce(g);
@@ -384,7 +394,7 @@ StepParams make_params(const lb_graph *g, int s) {
     p.child_dist = g->child_dist;
     p.n_children = g->phys_children;
     p.bitmap = g->bitmap;
-    p.epoch = g->epoch;
+    p.bm_words = bitmap_words(g->n);
     p.list_cap = s == LB_HP ? (g->list_cap < g->n ? g->list_cap : g->n) : g->list_cap;
     p.tile_cap = g->tile_cap;
     p.elist_cap = g->elist_cap;
@@ -393,6 +403,10 @@ StepParams make_params(const lb_graph *g, int s) {
     p.hp_threshold = g->opt.hp_threshold;
     p.hp_mode = g->opt.hp_mode;
     p.hp_warp_max = g->opt.hp_warp_max;
+    p.thread_max = g->opt.thread_max;
+    p.ns_mode = g->opt.ns_mode;
+    p.hp_depth = g->opt.hp_depth;
+    p.hist_bins = g->opt.hist_bins;
     p.strategy = s;
     p.use_cond = 0;
     return p;
@@ -401,12 +415,15 @@ StepParams make_params(const lb_graph *g, int s) {
 int step_grid(lb_graph *g, int s, bool sssp) {
     int &gr = g->grid[s][sssp ? 1 : 0];
     if (gr == 0) {
-        int occ = step_blocks_per_sm(s, sssp);
+        int occ = step_blocks_per_sm(s, sssp, g->opt.ns_mode);
         if (g->opt.ctas_per_sm > 0 && g->opt.ctas_per_sm < occ) occ = g->opt.ctas_per_sm;
         gr = occ * g->sms;
     }
     return gr;
 }
+
+// HP with a hierarchy deeper than one list runs k_hp_mdt before every step.
+bool hp_needs_mdt_kernel(const lb_graph *g, int s) { return s == LB_HP && g->opt.hp_depth > 1; }
 
 // Captures one step launch into the body of a conditional WHILE node.
 lb_status build_exec(lb_graph *g, int s, bool sssp, cudaGraphExec_t *out) {
@@ -440,7 +457,9 @@ lb_status build_exec(lb_graph *g, int s, bool sssp, cudaGraphExec_t *out) {
     const int grid = step_grid(g, s, sssp);
     e = cudaStreamBeginCaptureToGraph(g->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = launch_step(s, sssp, p, grid, g->stream);
+        cudaError_t le = cudaSuccess;
+        if (hp_needs_mdt_kernel(g, s)) le = launch_hp_mdt(p, 2 * g->sms, g->stream);
+        if (le == cudaSuccess) le = launch_step(s, sssp, p, grid, g->stream);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(g->stream, &captured);
         if (le != cudaSuccess) e = le;
@@ -489,6 +508,7 @@ lb_status run_query(lb_graph *g, int kind, int s, int32_t src, void *out_dev, in
         LB_CU(cudaGraphLaunch(ex, st));
     } else {
         for (;;) {
+            if (hp_needs_mdt_kernel(g, s)) LB_CU(launch_hp_mdt(p, 2 * g->sms, st));
             LB_CU(launch_step(s, sssp, p, grid, st));
             LB_CU(cudaMemcpyAsync(g->hflag, &g->ctl->active, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             LB_CU(cudaStreamSynchronize(st));
@@ -790,7 +810,7 @@ lb_status lb_mem_report(lb_graph *g, lb_strategy s, lb_mem_stats *out) {
     out->csr_weights = g->weighted ? 4 * (m > 0 ? m : 1) : 0;
     out->base_total = out->csr_offsets + out->csr_cols + out->csr_weights;
     out->status = 4 * n;
-    out->visited = 4 * ((n + 31) / 32) + 4 * n;
+    out->visited = 4 * 2 * bitmap_words(n);
     const int64_t tcap = round_tiles(m);
     if (s == LB_NS || s == LB_NS_PHYS || s == LB_HP) {
         LB_TRY(ensure_mdt(g));
@@ -828,36 +848,70 @@ lb_status lb_release_workspaces(lb_graph *g) {
 lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *srcs, int32_t nsrc, lb_options *best,
                       double *best_ms) {
     if (!g || !srcs || nsrc < 1 || nsrc > 1024) return fail(LB_ERR_ARG, "need a graph and 1..1024 sources");
-    if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP) return fail(LB_ERR_ARG, "bad kind");
+    if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP && kind != LB_TUNE_BOTH) return fail(LB_ERR_ARG, "bad kind");
     if (s == LB_AUTO) s = LB_WD;
     if ((int)s < 0 || (int)s >= kStrategies) return fail(LB_ERR_ARG, "unknown strategy");
     for (int32_t i = 0; i < nsrc; ++i)
         if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return fail(LB_ERR_ARG, "source out of range");
-    if (kind == LB_KIND_SSSP && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
+    if (kind != LB_KIND_BFS && !g->weighted) return fail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
     const lb_options base = g->opt;
-    // candidate grid: tile sizes and grid shapes for every strategy, plus the
-    // HP list-size threshold where it matters
-    const int32_t tiles[] = {1024, 2048, 4096, 8192, 16384};
-    const int32_t ctas[] = {0, 2, 3};
-    const int32_t thr[] = {256, 1024, 4096};
+    // candidate grid per strategy: block shapes (CTAs per SM the relax grid
+    // is sized for, the largest WD tile), the bin thresholds of the binned
+    // forms (edges a thread / a warp serves), the granule size of node
+    // splitting (MDT: the histogram's, or fixed), and HP's switch threshold
+    // and hierarchy depth
+    const int32_t ctas[] = {0, 2, 3, 4};
     std::vector<lb_options> cands;
-    for (int32_t t : tiles)
-        for (int32_t c : ctas) {
-            if (s == LB_HP) {
-                for (int32_t h : thr) {
-                    lb_options o = base;
-                    o.wd_tile = t;
-                    o.ctas_per_sm = c;
-                    o.hp_threshold = h;
-                    cands.push_back(o);
-                }
-            } else if (s == LB_WD || is_ep(s) || c == 0 || t == 8192) {
+    if (s == LB_WD) {
+        for (int32_t t : {2048, 4096, 8192, 16384})
+            for (int32_t c : ctas) {
                 lb_options o = base;
                 o.wd_tile = t;
                 o.ctas_per_sm = c;
                 cands.push_back(o);
             }
+    } else if (s == LB_HP) {
+        for (int32_t h : {256, 1024, 4096})
+            for (int32_t d : {1, 2, 3}) {
+                lb_options o = base;
+                o.hp_mode = 0;
+                o.hp_threshold = h;
+                o.hp_depth = d;
+                cands.push_back(o);
+            }
+        for (int32_t h : {256, 1024})
+            for (int32_t tm : {8, 32, 128})
+                for (int32_t wm : {512, 4096}) {
+                    lb_options o = base;
+                    o.hp_mode = 1;
+                    o.hp_threshold = h;
+                    o.thread_max = tm;
+                    o.hp_warp_max = wm;
+                    cands.push_back(o);
+                }
+    } else if (s == LB_NS || s == LB_NS_PHYS) {
+        for (int32_t md : {0, 32, 256, 2048}) {
+            lb_options o = base;
+            o.ns_mode = 0;
+            o.mdt_override = md;
+            cands.push_back(o);
         }
+        if (s == LB_NS)
+            for (int32_t md : {0, 256, 2048})
+                for (int32_t tm : {8, 32, 128}) {
+                    lb_options o = base;
+                    o.ns_mode = 1;
+                    o.mdt_override = md;
+                    o.thread_max = tm;
+                    cands.push_back(o);
+                }
+    } else {
+        for (int32_t c : ctas) {
+            lb_options o = base;
+            o.ctas_per_sm = c;
+            cands.push_back(o);
+        }
+    }
     double best_t = 1e300;
     lb_options best_o = base;
     uint32_t *out = nullptr;
@@ -879,13 +933,15 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
         if (so != LB_OK) return restore(so);
         double tot = 0.0;
         bool ok = true;
-        for (int32_t i = 0; i < nsrc && ok; ++i) {
+        for (int32_t i = 0; i < nsrc * (kind == LB_TUNE_BOTH ? 2 : 1) && ok; ++i) {
+            const int32_t k = kind == LB_TUNE_BOTH ? (i & 1) : kind;
+            const int32_t src = srcs[kind == LB_TUNE_BOTH ? i / 2 : i];
             for (int rep = 0; rep < 2 && ok; ++rep) {  // first run builds the loop; the second is timed
                 lb_status st;
                 {
                     std::lock_guard<std::mutex> lk(g->mu);
                     DeviceGuard dg(g->device);
-                    st = run_query(g, kind, s, srcs[i], out, nullptr, g->stream);
+                    st = run_query(g, k, s, src, out, nullptr, g->stream);
                 }
                 if (st != LB_OK) return restore(st);
                 lb_query_stats qs;

@@ -4,7 +4,8 @@
 //    dist[src] + weight; if dist[dst] > altdist: update dist, push dst"):
 //      BFS  - claim v with atomicOr on a visited bitmap, level[v] = L + 1;
 //      SSSP - atomicMin on dist[v]; queue v only for the first improvement
-//             in an iteration (stamp exchange), so a list never exceeds n.
+//             in an iteration (atomicOr on the iteration's queued bitmap),
+//             so a list never exceeds n.
 //    Both run test-then-atomic: the plain read can only be stale in the
 //    direction that costs an extra atomic, never one that loses an update.
 //  * Warp push buffers: the paper pushes with one atomic per node ("work
@@ -264,9 +265,39 @@ __device__ __forceinline__ bool bfs_claim(uint32_t *__restrict__ bitmap, uint32_
     return true;
 }
 
+// SSSP queued bits.  Iteration L sets the bit of every vertex it queues in
+// half (L & 1) of the bitmap and clears half ((L + 1) & 1), which no one
+// reads during iteration L, for iteration L + 1.  (A per-vertex stamp of
+// the queueing iteration would carry the same information in 32x the
+// bytes; these bits stay in L2 beside the distances.)
+__device__ __forceinline__ uint32_t *queued_half(uint32_t *bitmap, int64_t words, uint32_t level) {
+    return bitmap + (level & 1u) * words;
+}
+
+template <bool COH>
+__device__ __forceinline__ bool is_queued(const uint32_t *q, int32_t u) {
+    const uint32_t x = COH ? __ldcg(q + ((uint32_t)u >> 5)) : q[(uint32_t)u >> 5];
+    return (x >> ((uint32_t)u & 31u)) & 1u;
+}
+
+// Clears the other half of the queued bitmap with the whole grid: 16-byte
+// stores (words is a multiple of 4) when the half is 16-byte aligned, as
+// every allocation from cudaMalloc is; 4-byte stores otherwise.
+__device__ __forceinline__ void clear_next_queued(uint32_t *bitmap, int64_t words, uint32_t level) {
+    uint32_t *h = queued_half(bitmap, words, level + 1u);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (((uintptr_t)h & 15u) == 0) {
+        uint4 *q = reinterpret_cast<uint4 *>(h);
+        for (int64_t i = tid; i < words / 4; i += stride) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        for (int64_t i = tid; i < words; i += stride) h[i] = 0u;
+    }
+}
+
 // SSSP: true iff v improved and this is v's first queueing this iteration.
-__device__ __forceinline__ bool sssp_relax(uint32_t *__restrict__ status, uint32_t *__restrict__ epoch, int32_t v,
-                                           uint32_t du, uint32_t w, uint32_t stamp, Ctl *ctl) {
+__device__ __forceinline__ bool sssp_relax(uint32_t *__restrict__ status, uint32_t *__restrict__ q, int32_t v,
+                                           uint32_t du, uint32_t w, Ctl *ctl) {
     if (du == kInf) return false;
     const uint64_t a64 = (uint64_t)du + (uint64_t)w;
     const uint32_t alt = a64 >= kSat ? kSat : (uint32_t)a64;
@@ -274,18 +305,19 @@ __device__ __forceinline__ bool sssp_relax(uint32_t *__restrict__ status, uint32
     const uint32_t old = atomicMin(&status[v], alt);
     if (alt >= old) return false;
     if (alt == kSat) atomicOr(&ctl->error, kErrSaturated);
-    if (epoch[v] == stamp) return false;
-    return atomicExch(&epoch[v], stamp) != stamp;
+    if (is_queued<false>(q, v)) return false;
+    const uint32_t bit = 1u << ((uint32_t)v & 31u);
+    return !(atomicOr(&q[(uint32_t)v >> 5], bit) & bit);
 }
 
 // SSSP: distance a worklist entry u relaxes with.  When u has already been
-// queued again in this iteration (its stamp is the current one), its
-// distance improved after it was listed and the next iteration expands it
-// with that newer value, so expanding it now is redundant work: return
-// kInf, which makes every relaxation from u a no-op.
-__device__ __forceinline__ uint32_t sssp_source_dist(const uint32_t *__restrict__ status,
-                                                     const uint32_t *__restrict__ epoch, int32_t u, uint32_t stamp) {
-    return epoch[u] == stamp ? kInf : status[u];
+// queued again in this iteration (its bit is set), its distance improved
+// after it was listed and the next iteration expands it with that newer
+// value, so expanding it now is redundant work: return kInf, which makes
+// every relaxation from u a no-op.
+__device__ __forceinline__ uint32_t sssp_source_dist(const uint32_t *__restrict__ status, const uint32_t *q,
+                                                     int32_t u) {
+    return is_queued<false>(q, u) ? kInf : status[u];
 }
 
 // Relaxes ITEMS loaded edges of a warp and pushes the vertices that must be
@@ -311,8 +343,8 @@ template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false, bool FLU
 __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32_t (&vv)[ITEMS],
                                             const uint32_t (&ww)[ITEMS], const uint32_t (&dd)[ITEMS],
                                             const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
-                                            uint32_t *__restrict__ epoch, uint32_t *__restrict__ status,
-                                            uint32_t level, uint32_t stamp, uint32_t *err, WarpBuf &wb,
+                                            uint32_t *__restrict__ qcur, uint32_t *__restrict__ status,
+                                            uint32_t level, uint32_t *err, WarpBuf &wb,
                                             WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
     bool cand[ITEMS];
     uint32_t val[ITEMS];
@@ -355,13 +387,13 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
         // queue only the first improvement of v in this iteration
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it)
-            if (won[it] && ld_mut<COH>(epoch + vv[it]) == stamp) won[it] = false;
+            if (won[it] && is_queued<COH>(qcur, vv[it])) won[it] = false;
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it)
-            if (won[it]) prev[it] = atomicExch(&epoch[vv[it]], stamp);
+            if (won[it]) prev[it] = atomicOr(&qcur[(uint32_t)vv[it] >> 5], 1u << ((uint32_t)vv[it] & 31u));
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it)
-            if (won[it] && prev[it] == stamp) won[it] = false;
+            if (won[it] && (prev[it] & (1u << ((uint32_t)vv[it] & 31u)))) won[it] = false;
     }
     // offsets are < m < 2^31 (checked when the graph is created)
     int32_t vb[ITEMS], ve[ITEMS];
@@ -394,6 +426,69 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
         wpush(wb, cnt, want, vv[it], vb[it], (uint32_t)(ve[it] - vb[it]));
         if (FLUSH && cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
     }
+}
+
+// BFS relax of R loaded edges per lane with warp-uniform early exits: the
+// visited check for every item, then (only if some lane of the warp found
+// an unvisited vertex) the claims, then (only if some lane won one) the
+// level writes, offset loads and one push of all won vertices with edges.
+// The push buffer is flushed only when this group's pushes would not fit,
+// so flushes carry close to kWB entries.  Requires R * 32 <= kWB.
+template <int R, bool COH>
+__device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_t (&vv)[R],
+                                               const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
+                                               uint32_t *__restrict__ status, uint32_t level, WarpBuf &wb,
+                                               WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    static_assert(R * 32 <= kWB, "push buffer too small for one group");
+    uint32_t cand = 0;  // bit r: item r found v unvisited
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t x = ok[r] ? ld_mut<COH || LB_BFS_BITMAP_CG>(bitmap + ((uint32_t)vv[r] >> 5)) : 0xFFFFFFFFu;
+        if (!((x >> ((uint32_t)vv[r] & 31u)) & 1u)) cand |= 1u << r;
+    }
+    if (!__any_sync(kFull, cand != 0u)) return;
+    uint32_t won = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if ((cand >> r) & 1u) {
+            const uint32_t bit = 1u << ((uint32_t)vv[r] & 31u);
+            if (!(atomicOr(bitmap + ((uint32_t)vv[r] >> 5), bit) & bit)) won |= 1u << r;
+        }
+    }
+    if (!__any_sync(kFull, won != 0u)) return;
+    int32_t vb[R], vd[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        vb[r] = 0;
+        vd[r] = 0;
+        if ((won >> r) & 1u) {
+            status[vv[r]] = level + 1;
+            // offsets are < m < 2^31 (checked when the graph is created)
+            vb[r] = (int32_t)__ldg(off + vv[r]);
+            vd[r] = (int32_t)__ldg(off + vv[r] + 1) - vb[r];
+        }
+    }
+    unsigned bal[R];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        bal[r] = __ballot_sync(kFull, ((won >> r) & 1u) && vd[r] > 0);
+        tot += __popc(bal[r]);
+    }
+    if (tot == 0) return;
+    if (cnt + tot > (uint32_t)kWB) wflush<kOutNode, true>(wb, ws, cnt, o);
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if ((bal[r] >> lane_id()) & 1u) {
+            const uint32_t s = cnt + __popc(bal[r] & lt);
+            wb.v[s] = vv[r];
+            wb.beg[s] = vb[r];
+            wb.deg[s] = (uint32_t)vd[r];
+        }
+        cnt += __popc(bal[r]);
+    }
+    __syncwarp();
 }
 
 // ---- end-of-step protocol ----------------------------------------------------
@@ -444,7 +539,6 @@ __device__ __forceinline__ void set_loop(const StepParams &p, Ctl *ctl, bool mor
         more = false;
     }
     ctl->active = more ? 1u : 0u;
-    if (!more) ctl->epoch_next = ctl->epoch_base + ctl->level + 1;
     if (p.use_cond) cudaGraphSetConditional(p.cond, more ? 1u : 0u);
 }
 

@@ -2,8 +2,12 @@
 //
 // Data layout in HBM (one query workspace per graph, reused by every query):
 //   status[n]        uint32 level / distance, 0xFFFFFFFF = not reached
-//   bitmap[n/32]     BFS visited bits (claimed with atomicOr)
-//   epoch[n]         SSSP stamp of the iteration that last queued a vertex
+//   bitmap[2 W]      W = ceil(n/32) rounded up to a multiple of 4 words.
+//                    BFS: words 0..W-1 are the visited bits (claimed with
+//                    atomicOr).  SSSP: the two halves are the "queued in
+//                    this iteration" bits of even and odd iterations; an
+//                    iteration sets bits in its own half and clears the
+//                    other one, which the next iteration uses
 //   node lists x2    worklist entries {v, beg, scan: int32 each} plus
 //                    tstart[] (first entry of every WD tile); double-buffered
 //   sub lists x2     HP sub-worklists, same layout
@@ -24,6 +28,7 @@ constexpr uint32_t kSat = 0xFFFFFFFEu;  // saturated distance (>= 2^32 - 2)
 constexpr int kBlock = 256;             // threads per CTA of every step kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kTraceMax = 4096;
+constexpr int kHistMax = 4096;  // largest HistogramBinCount
 // Tile starts are recorded every kTileGrain worklist edges; an iteration
 // then cuts its list into tiles of q * kTileGrain edges, q chosen from the
 // list's size so that small lists still spread over many CTAs.
@@ -70,13 +75,15 @@ struct Ctl {
     unsigned long long sub_pack;  // HP sub-list output: (entries << 32) | edges
     uint32_t hp_kind;   // HP: next step is a sub-iteration (1), WD (2) or binned (3)
     uint32_t hp_sub;    // HP: sub-iteration index inside the super-iteration
+    uint32_t hp_mdt;    // HP: edges per node in the next sub-iteration
+    uint32_t hp_lvl;    // HP: position of the input list in the super-iteration's chain
+    uint32_t hp_mdt_pending;  // HP: the input sub-list needs its own MDT (k_hp_mdt)
+    uint32_t hp_pad;
+    unsigned long long sub_maxdeg;  // HP: largest remaining degree pushed to the sub-list
     uint32_t sub_in;    // HP: sub list buffer read when hp_from == kHpFromSub
     uint32_t blocks_done;
     uint32_t active;    // loop condition
     uint32_t error;
-    uint32_t epoch_base;    // SSSP: iteration i stamps epoch_base + i
-    uint32_t epoch_next;    // first stamp free for the next query
-    uint32_t epoch_reset;   // init kernel must clear the stamp array
     uint32_t max_levels;
     uint64_t max_steps;
     uint64_t step;
@@ -87,6 +94,7 @@ struct Ctl {
     uint32_t trace_len;
     uint32_t pad;
     TraceRec trace[kTraceMax];
+    uint32_t hp_hist[kHistMax];  // HP depth > 1: histogram of a sub-list (zero between uses)
 };
 
 struct GraphDev {
@@ -113,8 +121,8 @@ struct StepParams {
     NodeList subs[2];
     int32_t *elist[2];
     const int32_t *coo_src;
-    uint32_t *bitmap;
-    uint32_t *epoch;
+    uint32_t *bitmap;            // 2 * bm_words words (see the layout above)
+    int64_t bm_words;            // W: words per bitmap half, a multiple of 4
     const int32_t *child_first;  // NS_PHYS: first child id of a split node, -1 if not split
     const int32_t *parent_of;    // NS_PHYS: parent of child n + i
     uint32_t *child_dist;        // NS_PHYS: mirrored distance of child n + i
@@ -126,7 +134,11 @@ struct StepParams {
     int32_t mdt;
     int32_t hp_threshold;  // <= 0: never switch to WD
     int32_t hp_mode;       // 0: sub-iterations, 1: degree-binned steps
-    int32_t hp_warp_max;   // hp_mode 1: largest degree a warp serves
+    int32_t hp_warp_max;   // binned forms: largest entry a warp serves
+    int32_t thread_max;    // binned forms: largest entry a thread serves
+    int32_t ns_mode;       // 0: thread per granule, 1: binned granules
+    int32_t hp_depth;      // HP: lists of a super-iteration's chain with their own MDT
+    int32_t hist_bins;     // HistogramBinCount of the MDT heuristic
     int32_t strategy;
     int32_t use_cond;
     int32_t pad;
@@ -135,10 +147,11 @@ struct StepParams {
 
 // ---- launch entry points implemented by the strategy translation units --
 cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, cudaStream_t st);
-int step_blocks_per_sm(int strategy, bool sssp);
+int step_blocks_per_sm(int strategy, bool sssp, int ns_mode);
 cudaError_t launch_prepare(const StepParams &p, int32_t src, uint32_t *status, int kind, uint32_t max_levels,
                            uint64_t max_steps, uint64_t time_limit_ns, cudaStream_t st);
 cudaError_t launch_init(const StepParams &p, int grid, cudaStream_t st);
+cudaError_t launch_hp_mdt(const StepParams &p, int grid, cudaStream_t st);
 cudaError_t launch_finish_query(const StepParams &p, cudaStream_t st);
 cudaError_t launch_coo_build(const GraphDev &g, int32_t *coo_src, cudaStream_t st);
 cudaError_t launch_mdt(const GraphDev &g, int32_t bins, unsigned long long *scratch, int64_t *result,

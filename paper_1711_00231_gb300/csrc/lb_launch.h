@@ -23,6 +23,8 @@ constexpr int kItemsEp = LB_EP_ITEMS;  // worklist edges per thread per round in
 
 cudaError_t launch_step_entry(bool sssp, bool granules, const StepParams &p, int grid, cudaStream_t st);
 int occupancy_step_entry(bool sssp, bool granules);
+cudaError_t launch_step_ns_binned(bool sssp, const StepParams &p, int grid, cudaStream_t st);
+int occupancy_step_ns_binned(bool sssp);
 cudaError_t launch_step_phys(bool sssp, const StepParams &p, int grid, cudaStream_t st);
 int occupancy_step_phys(bool sssp);
 cudaError_t launch_step_wd(bool sssp, const StepParams &p, int grid, cudaStream_t st);

@@ -39,13 +39,13 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // byte offsets of the pieces inside the scratch array
 constexpr size_t kOffCtl = 0;
 constexpr size_t kOffBitmap = align256(kOffCtl + sizeof(Ctl));
-constexpr size_t kOffEpoch = align256(kOffBitmap + sizeof(uint32_t) * (size_t)((kNaMaxN + 31) / 32));
+constexpr int64_t kNaBitmapWords = ((kNaMaxN + 31) / 32 + 3) / 4 * 4;  // the BFS visited bits
 constexpr size_t kListV = align256(sizeof(int32_t) * (size_t)kNaMaxN);
 constexpr size_t kListBeg = align256(sizeof(int32_t) * (size_t)kNaMaxN);
 constexpr size_t kListScan = align256(sizeof(int32_t) * (size_t)(kNaMaxN + 1));
 constexpr size_t kListTiles = align256(sizeof(int32_t) * (size_t)kNaTiles);
 constexpr size_t kListBytes = kListV + kListBeg + kListScan + kListTiles;
-constexpr size_t kOffValid = align256(kOffEpoch + sizeof(uint32_t));  // one stamp word: BFS needs no stamps
+constexpr size_t kOffValid = align256(kOffBitmap + sizeof(uint32_t) * (size_t)kNaBitmapWords);
 constexpr size_t kOffLists = align256(kOffValid + sizeof(uint32_t));
 constexpr size_t kNaBytes = kOffLists + 2 * kListBytes;
 
@@ -104,7 +104,7 @@ extern "C" lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t
     p.g = GraphDev{offsets_dev, cols_dev, nullptr, n, m};
     p.ctl = (Ctl *)(base + kOffCtl);
     p.bitmap = (uint32_t *)(base + kOffBitmap);
-    p.epoch = (uint32_t *)(base + kOffEpoch);
+    p.bm_words = kNaBitmapWords;  // BFS reads only the first half: no second half is held
     for (int b = 0; b < 2; ++b) {
         unsigned char *L = base + kOffLists + (size_t)b * kListBytes;
         p.lists[b].v = (int32_t *)L;
@@ -119,7 +119,7 @@ extern "C" lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t
     p.hp_threshold = 0;
     p.strategy = LB_WD;
     p.use_cond = 0;
-    const int grid = step_blocks_per_sm(LB_WD, false) * sms;
+    const int grid = step_blocks_per_sm(LB_WD, false, 0) * sms;
     cudaStream_t st = (cudaStream_t)stream;
     // the caller's CSR shape, checked before the traversal indexes with it
     uint32_t *verr = (uint32_t *)(base + kOffValid);

@@ -1,8 +1,8 @@
 // Batched / served queries: one persistent kernel runs many BFS / SSSP
 // queries over many resident graphs at once.
 //
-// Every query in flight owns a slot: its own worklists, visited bitmap,
-// stamps and loop state.  A slot always has at most one open job (reset its
+// Every query in flight owns a slot: its own worklists, visited / queued
+// bitmaps and loop state.  A slot always has at most one open job (reset its
 // output, relax one worklist iteration with workload-decomposition tiles,
 // or check for overflow), cut into tiles.  The CTAs of the persistent grid
 // scan the slots and claim tiles with one atomicAdd on the slot's claim word
@@ -21,8 +21,8 @@
 // is pending or in flight, and the queries continue from the slots' state.
 //
 // All loads of data other CTAs write during the kernel (worklists, status,
-// bitmap, stamps) bypass L1 (ld.global.cg), because L1 is not coherent
-// within a kernel and slots are reused.
+// bitmaps) bypass L1 (ld.global.cg), because L1 is not coherent within a
+// kernel and slots are reused.
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -138,9 +138,7 @@ struct Slot {
     uint32_t par;
     uint32_t in_cnt;
     uint32_t error;
-    uint32_t epoch_base;
-    uint32_t epoch_next;
-    uint32_t epoch_reset;
+    uint32_t pad;
     uint64_t in_edges;
     unsigned long long out_pack;
     unsigned long long relaxed;
@@ -148,8 +146,7 @@ struct Slot {
     unsigned long long ticket;
     unsigned long long t_admit;
     uint32_t *status;
-    uint32_t *bitmap;
-    uint32_t *epoch;
+    uint32_t *bitmap;  // 2 x Params::bm_words: BFS visited bits / SSSP queued bits (even, odd iterations)
     NodeList lists[2];
 };
 
@@ -177,6 +174,7 @@ struct Params {
     int64_t slot_cap;   // worklist entries per slot list
     int64_t tile_cap;   // tile starts per slot list
     int64_t slot_n;     // largest n a slot serves
+    int64_t bm_words;   // words per half of a slot's bitmap (a multiple of 4)
     uint64_t idle_ns;
     uint64_t hard_ns;
 };
@@ -226,8 +224,8 @@ __device__ __forceinline__ bool bfs_claim_cg(uint32_t *bitmap, uint32_t *status,
     return true;
 }
 
-__device__ __forceinline__ bool sssp_relax_cg(uint32_t *status, uint32_t *epoch, int32_t v, uint32_t du, uint32_t w,
-                                              uint32_t stamp, uint32_t *err) {
+__device__ __forceinline__ bool sssp_relax_cg(uint32_t *status, uint32_t *q, int32_t v, uint32_t du, uint32_t w,
+                                              uint32_t *err) {
     if (du == kInf) return false;
     const uint64_t a64 = (uint64_t)du + (uint64_t)w;
     const uint32_t alt = a64 >= kSat ? kSat : (uint32_t)a64;
@@ -235,8 +233,9 @@ __device__ __forceinline__ bool sssp_relax_cg(uint32_t *status, uint32_t *epoch,
     const uint32_t old = atomicMin(&status[v], alt);
     if (alt >= old) return false;
     if (alt == kSat) atomicOr(err, kErrSaturated);
-    if (__ldcg(epoch + v) == stamp) return false;
-    return atomicExch(&epoch[v], stamp) != stamp;
+    if (is_queued<true>(q, v)) return false;
+    const uint32_t bit = 1u << ((uint32_t)v & 31u);
+    return !(atomicOr(&q[(uint32_t)v >> 5], bit) & bit);
 }
 
 // Dynamic slot fields change between jobs and are written by other SMs, so
@@ -244,7 +243,7 @@ __device__ __forceinline__ bool sssp_relax_cg(uint32_t *status, uint32_t *epoch,
 // fixed at server creation.
 struct SlotState {
     int32_t graph, src, kind;
-    uint32_t level, par, in_cnt, epoch_base, epoch_reset;
+    uint32_t level, par, in_cnt;
     uint64_t in_edges;
     uint32_t *status;
 };
@@ -258,8 +257,6 @@ __device__ __forceinline__ SlotState slot_state(const Slot *S) {
     t.level = V->level;
     t.par = V->par;
     t.in_cnt = V->in_cnt;
-    t.epoch_base = V->epoch_base;
-    t.epoch_reset = V->epoch_reset;
     t.in_edges = V->in_edges;
     t.status = V->status;
     return t;
@@ -292,7 +289,6 @@ __device__ void complete_query(const Params &P, Slot *S, int32_t status_code) {
     d->edges_relaxed = V->relaxed;
     __threadfence_system();
     st_release_sys(&d->seq, idx + 1ull);
-    S->epoch_next = V->epoch_base + V->level + 1;
     const unsigned long long jw = atomicAdd(&S->job, 0ull);
     atomicExch(&S->job, job_word(job_gen(jw), kJobNone, 0u, 0u));
     __threadfence();
@@ -383,16 +379,14 @@ __device__ void init_tile(const Params &P, Slot *S, int64_t k) {
     const int64_t v1 = min(v0 + kInitChunk, g.n);
     const int32_t src = st.src;
     const bool sssp = st.kind == 1;
-    const bool reset_epoch = st.epoch_reset != 0;
     uint32_t *status = st.status;
-    for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
-        status[i] = i == src ? 0u : kInf;
-        if (sssp && reset_epoch) S->epoch[i] = 0u;
-    }
-    if (!sssp) {
-        const int64_t w0 = v0 / 32, w1 = (v1 + 31) / 32;
-        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x)
-            S->bitmap[w] = w == (src >> 5) ? (1u << (src & 31)) : 0u;
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) status[i] = i == src ? 0u : kInf;
+    // BFS: this chunk's visited bits; SSSP: its queued bits in both halves
+    // (kInitChunk is a multiple of 32, so chunks own whole words)
+    const int64_t w0 = v0 / 32, w1 = (v1 + 31) / 32;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        S->bitmap[w] = (!sssp && w == (src >> 5)) ? (1u << (src & 31)) : 0u;
+        if (sssp) S->bitmap[P.bm_words + w] = 0u;
     }
 }
 
@@ -406,9 +400,27 @@ __device__ void check_tile(const Params &P, Slot *S, int64_t k) {
 }
 
 template <bool SSSP>
-__device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t q, WarpBuf &wb, WarpScratch &ws) {
+__device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, int64_t q, WarpBuf &wb,
+                           WarpScratch &ws) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
+    uint32_t *qcur = queued_half(S->bitmap, P.bm_words, st.level);
+    if (SSSP) {
+        // The other half still holds the bits of the previous iteration,
+        // whose queued vertices are exactly this iteration's list entries
+        // (a vertex without out-edges is queued but never listed; its stale
+        // bit is harmless, as such a vertex is never listed or expanded).
+        // Tile t clears the bits of its share of the entries for the next
+        // iteration, which starts only after every tile of this one.
+        uint32_t *qn = queued_half(S->bitmap, P.bm_words, st.level + 1u);
+        const int64_t per = ((int64_t)st.in_cnt + ntiles - 1) / ntiles;
+        const int64_t k0 = t * per, k1 = min(k0 + per, (int64_t)st.in_cnt);
+        const int32_t *vin = S->lists[st.par].v;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            const int32_t u = __ldcg(vin + k);
+            if (u >= 0 && (int64_t)u < g.n) atomicAnd(&qn[(uint32_t)u >> 5], ~(1u << ((uint32_t)u & 31u)));
+        }
+    }
     FlushOut o;
     o.list = S->lists[st.par ^ 1u];
     o.elist = nullptr;
@@ -422,8 +434,7 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t q, WarpB
     o.child_first = nullptr;
     uint32_t cnt = 0;
     wd_walk_tile<SSSP, kItems, true>(g, S->lists[st.par], st.in_cnt, (int64_t)st.in_edges, q * kTileGrain, t,
-                                     S->bitmap, S->epoch, st.status, st.level, st.epoch_base + st.level, &S->error, wb,
-                                     ws, cnt, o);
+                                     S->bitmap, qcur, st.status, st.level, &S->error, wb, ws, cnt, o);
 #if LB_BLOCK_FLUSH
     wflush_block<kOutNode, true>(wb, ws, cnt, o);
 #else
@@ -468,13 +479,6 @@ __device__ void admit(const Params &P) {
         if (valid) {
             const GraphDev g = P.graphs[r.graph];
             valid = r.src >= 0 && (int64_t)r.src < g.n && g.n <= P.slot_n && (r.kind == 0 || g.w != nullptr);
-        }
-        if (S->epoch_next == 0u || S->epoch_next > 0xF0000000u) {
-            S->epoch_reset = 1;
-            S->epoch_base = 1;
-        } else {
-            S->epoch_reset = 0;
-            S->epoch_base = S->epoch_next;
         }
         S->busy = 1;
         atomicAdd(&sh->active, 1u);
@@ -671,8 +675,9 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
         const uint32_t kind = s_kind;
         if (kind == kJobInit) init_tile(P, S, s_tile);
         else if (kind == kJobCheck) check_tile(P, S, s_tile);
-        else if (((const volatile Slot *)S)->kind == 1) relax_tile<true>(P, S, s_tile, s_q, s_wb[warp], s_ws[warp]);
-        else relax_tile<false>(P, S, s_tile, s_q, s_wb[warp], s_ws[warp]);
+        else if (((const volatile Slot *)S)->kind == 1)
+            relax_tile<true>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
+        else relax_tile<false>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
         // Other CTAs read this tile's stores (list entries, resets) in the
         // slot's next job within this same kernel: they are made visible
         // device-wide before the tile is counted as done.
@@ -754,6 +759,7 @@ struct lb_server {
     std::vector<void *> bufs;      // slot workspace allocations
     int32_t nslots = 0;
     int64_t slot_n = 0, slot_m = 0, slot_cap = 0, tile_cap = 0;
+    int64_t bm_words = 0;  // words per half of a slot's bitmap
     int64_t slot_bytes = 0;
     int grid = 0;
     cudaStream_t stream = nullptr;
@@ -823,6 +829,7 @@ lb_status launch_kernel(lb_server *s) {
     P.slot_cap = s->slot_cap;
     P.tile_cap = s->tile_cap;
     P.slot_n = s->slot_n;
+    P.bm_words = s->bm_words;
     P.idle_ns = (uint64_t)s->opt.idle_us * 1000ull;
     P.hard_ns = (uint64_t)s->opt.launch_ms * 1000000ull;  // one persistent launch never outlives this
     k_serve_t0<<<1, 1, 0, s->stream>>>(s->d_shared);
@@ -900,9 +907,10 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     }
     s->slot_cap = s->slot_n;
     s->tile_cap = s->slot_m / kTileGrain + 2;
-    // per slot: bitmap + stamps + two worklists (v, beg, scan, tile starts)
+    // per slot: two bitmaps + two worklists (v, beg, scan, tile starts)
+    s->bm_words = ((s->slot_n + 31) / 32 + 3) / 4 * 4;
     const int64_t per_list = 4 * s->slot_cap + 4 * s->slot_cap + 4 * (s->slot_cap + 1) + 4 * s->tile_cap;
-    s->slot_bytes = 4 * ((s->slot_n + 31) / 32) + 4 * s->slot_n + 2 * per_list + 4096;
+    s->slot_bytes = 4 * 2 * s->bm_words + 2 * per_list + 4096;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     int64_t fit = (int64_t)((double)free_b * o.mem_fraction) / (s->slot_bytes > 0 ? s->slot_bytes : 1);
@@ -938,9 +946,7 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
             e = cudaMalloc(p, bytes);
             if (e == cudaSuccess) s->bufs.push_back(*p);
         };
-        get((void **)&S.bitmap, 4 * (size_t)((s->slot_n + 31) / 32));
-        get((void **)&S.epoch, 4 * (size_t)s->slot_n);
-        if (e == cudaSuccess) e = cudaMemset(S.epoch, 0, 4 * (size_t)s->slot_n);
+        get((void **)&S.bitmap, 4 * 2 * (size_t)s->bm_words);
         for (int b = 0; b < 2; ++b) {
             get((void **)&S.lists[b].v, 4 * (size_t)s->slot_cap);
             get((void **)&S.lists[b].beg, 4 * (size_t)s->slot_cap);

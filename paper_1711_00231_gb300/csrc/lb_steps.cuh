@@ -25,7 +25,7 @@
 #define LB_WD_FAST_SSSP 1
 #endif
 // Column and weight streams loaded evict-first (ld.global.cs) so the
-// randomly read distance, stamp and visited lines keep their place in L2
+// randomly read distance, queued and visited lines keep their place in L2
 // (bit mask: 1 = SSSP, 2 = BFS).  Measured on R-MAT scale 24: SSSP 3.7%
 // faster, BFS unchanged.
 #ifndef LB_WD_STREAM
@@ -46,6 +46,17 @@ __device__ __forceinline__ T ld_edge(const T *p) {
 #endif
 #ifndef LB_WD_IDX32
 #define LB_WD_IDX32 1
+#endif
+// BFS walks with wd_walk_bfs (a 64-entry window of the list in registers,
+// the lean relax) instead of wd_walk_tile32.
+#ifndef LB_BFS_WALK2
+#define LB_BFS_WALK2 0
+#endif
+// BFS walk relaxes with relax_bfs_lean (warp-uniform early exits, one push
+// per group, flushes only when a group's pushes would not fit) instead of
+// the staged relax shared with SSSP.
+#ifndef LB_BFS_LEAN
+#define LB_BFS_LEAN 0
 #endif
 
 // The final flush of a WD iteration (and of a serving RELAX tile) as one
@@ -85,7 +96,8 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
     const uint32_t par = ctl->par;
     const int64_t in_cnt = ctl->in_cnt;
     const uint32_t level = ctl->level;
-    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+    if (SSSP) clear_next_queued(p.bitmap, p.bm_words, level);
     uint32_t *status = ctl->status;
     const NodeList in = p.lists[par];
     FlushOut o;
@@ -114,7 +126,7 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
                 atomicOr(&ctl->error, kErrBounds);
                 cur = end = 0;
             } else if (SSSP) {
-                du = sssp_source_dist(status, p.epoch, __ldg(in.v + i), stamp);
+                du = sssp_source_dist(status, qcur, __ldg(in.v + i));
             }
         }
         while (__any_sync(kFull, cur < end)) {
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_step_entry(StepParams p) {
             uint32_t vd = 0;
             if (cur < end) {
                 v = __ldg(p.g.col + cur);
-                const bool hit = SSSP ? sssp_relax(status, p.epoch, v, du, __ldg(p.g.w + cur), stamp, ctl)
+                const bool hit = SSSP ? sssp_relax(status, qcur, v, du, __ldg(p.g.w + cur), ctl)
                                       : bfs_claim(p.bitmap, status, v, level + 1);
                 if (hit) {
                     vb = __ldg(p.g.off + v);
@@ -159,7 +171,8 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
     const uint32_t par = ctl->par;
     const int64_t in_cnt = ctl->in_cnt;
     const uint32_t level = ctl->level;
-    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+    if (SSSP) clear_next_queued(p.bitmap, p.bm_words, level);
     uint32_t *status = ctl->status;
     const int64_t n = p.g.n;
     const NodeList in = p.lists[par];
@@ -193,10 +206,10 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
                 cur = end = 0;
             } else if (SSSP) {
                 if ((int64_t)x < n) {
-                    du = sssp_source_dist(status, p.epoch, x, stamp);
+                    du = sssp_source_dist(status, qcur, x);
                 } else {
                     const int32_t parent = __ldg(p.parent_of + (x - n));
-                    du = p.epoch[parent] == stamp ? kInf : p.child_dist[x - n];
+                    du = is_queued<false>(qcur, parent) ? kInf : p.child_dist[x - n];
                 }
             }
         }
@@ -221,7 +234,9 @@ __global__ void __launch_bounds__(kBlock) k_step_phys(StepParams p) {
                                 const int64_t nk = ((int64_t)vd + mdt - 1) / mdt - 1;
                                 for (int64_t c = 0; c < nk; ++c) atomicMin(&p.child_dist[cf - n + c], alt);
                             }
-                            want = vd > 0 && p.epoch[v] != stamp && atomicExch(&p.epoch[v], stamp) != stamp;
+                            want = vd > 0 && !is_queued<false>(qcur, v) &&
+                                   !(atomicOr(&qcur[(uint32_t)v >> 5], 1u << ((uint32_t)v & 31u)) &
+                                     (1u << ((uint32_t)v & 31u)));
                         }
                     }
                 } else if (bfs_claim(p.bitmap, status, v, level + 1)) {
@@ -290,8 +305,8 @@ __device__ __forceinline__ KT warp_search(const int32_t *scan, KT lo, KT hi, IT 
 // wraps mod 2^32).  Used for BFS.
 template <bool SSSP, int STEPS, bool COH>
 __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
-                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
-                                             uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
+                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
+                                             uint32_t *status, uint32_t level, uint32_t *err,
                                              WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
     const int64_t q = T / kTileGrain;
     const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
@@ -331,7 +346,7 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
     // (most edges of a skewed graph) load no list entries at all
     constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
     constexpr int R = STEPS;
-    static_assert(32 * R <= kWB - 32, "push buffer too small for one group");
+    static_assert(32 * R <= kWB - ((!SSSP && LB_BFS_LEAN) ? 0 : 32), "push buffer too small for one group");
     int32_t sj = INT32_MAX, bj = 0, uj = 0;
     bool fresh = false;
     // the walk produces one group of R x 32 edges per pass, either from a
@@ -379,7 +394,7 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
                 in_run = true;
                 if ((LB_WD_PREFETCH & 1) && !SSSP && lane == 0 && rend - ew > (IT)(32 * R))
                     bulk_prefetch_l2(g.col + (rbase + ew + (IT)(32 * R)), g.col + (rbase + rend), g.col + g.m);
-                if (SSSP) rdu = ld_mut<COH>(epoch + ucur) == stamp ? kInf : ld_mut<COH>(status + ucur);
+                if (SSSP) rdu = is_queued<COH>(qcur, ucur) ? kInf : ld_mut<COH>(status + ucur);
             }
         }
         if (in_run) {
@@ -455,16 +470,136 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
                         vv[st] = ld_edge<SSSP>(g.col + eidx);
                         if (SSSP) {
                             ww[st] = ld_edge<SSSP>(g.w + eidx);
-                            dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
+                            dd[st] = is_queued<COH>(qcur, u_l) ? kInf : ld_mut<COH>(status + u_l);
                         }
                     }
                 }
             }
             ew += (IT)(32 * R);
         }
-        if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
-        relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
-                                                         err, wb, ws, cnt, o);
+        if constexpr (!SSSP && LB_BFS_LEAN) {
+            relax_bfs_lean<R, COH>(ok, vv, g.off, bitmap, status, level, wb, ws, cnt, o);
+        } else {
+            if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
+            relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, qcur, status, level, err,
+                                                             wb, ws, cnt, o);
+        }
+    }
+}
+
+// BFS walk of one tile with a 64-entry window of the list in registers.
+// Lane l holds entries kb + l and kb + 32 + l (first list edge s and the
+// delta d = first CSR edge - s, so an edge's CSR index is d + list edge);
+// the current entry kcur stays within the window's first half, and the
+// window slides by 32 entries when kcur leaves it (one reload per 32
+// entries, not per step).  A group of R x 32 edges that lies inside entry
+// kcur is loaded directly; otherwise each 32-edge step finds every lane's
+// entry from the bit mask of entry starts inside the step (an entry has at
+// least one edge, so at most 32 start in 32 positions).  The relax is
+// relax_bfs_lean.  32-bit list edges and edge ids (< 2^31).
+template <int R, bool COH>
+__device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
+                                            int64_t T, int64_t t, uint32_t *bitmap, uint32_t *status,
+                                            uint32_t level, uint32_t *err, WarpBuf &wb, WarpScratch &ws,
+                                            uint32_t &cnt, const FlushOut &o) {
+    const int64_t q = T / kTileGrain;
+    const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
+    const int64_t ntiles = (E + T - 1) / T;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
+    const int64_t e0 = t * T;
+    const int64_t e1 = min(e0 + T, E);
+    const int64_t i0 = ld_list<COH>(in.tstart + t * q);
+    const int64_t ihi =
+        (t + 1 < ntiles) ? min((int64_t)ld_list<COH>(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
+    if (i0 < 0 || i0 >= ihi) {
+        if (lane == 0) atomicOr(err, kErrBounds);
+        return;
+    }
+    const int64_t w064 = e0 + (int64_t)warp * W;
+    if (w064 >= e1) return;  // warp-uniform
+    const int32_t w0 = (int32_t)w064;
+    const int32_t w1 = (int32_t)min(w064 + W, e1);
+    const int32_t ihiK = (int32_t)ihi;
+    const int32_t m = (int32_t)g.m;
+    int32_t kcur = warp_search<COH, uint32_t, int32_t>(in.scan, (int32_t)i0, ihiK, (uint32_t)w0, lane);
+    int32_t kb = kcur;
+    int32_t s0 = INT32_MAX, d0 = 0, s1 = INT32_MAX, d1 = 0;
+    {
+        const int32_t j0 = kb + (int32_t)lane, j1 = j0 + 32;
+        if (j0 < ihiK) { s0 = ld_list<COH>(in.scan + j0); d0 = ld_list<COH>(in.beg + j0) - s0; }
+        if (j1 < ihiK) { s1 = ld_list<COH>(in.scan + j1); d1 = ld_list<COH>(in.beg + j1) - s1; }
+    }
+    int32_t ew = w0;
+    while (ew < w1) {  // warp-uniform
+        bool ok[R];
+        int32_t vv[R];
+        if (kcur >= kb + 32) {  // slide: the second half becomes the first
+            kb += 32;
+            s0 = s1;
+            d0 = d1;
+            const int32_t j1 = kb + 32 + (int32_t)lane;
+            s1 = INT32_MAX;
+            d1 = 0;
+            if (j1 < ihiK) { s1 = ld_list<COH>(in.scan + j1); d1 = ld_list<COH>(in.beg + j1) - s1; }
+        }
+        // start of entry kcur + 1 (window position 1..32)
+        const int32_t pn = kcur + 1 - kb;
+        const int32_t s_next = __shfl_sync(kFull, pn < 32 ? s0 : s1, pn & 31);
+        if (s_next >= ew + 32 * R) {
+            // the whole group lies inside entry kcur
+            const int32_t pc = kcur - kb;
+            const int32_t dcur = __shfl_sync(kFull, d0, pc);
+            if (dcur + ew < 0 || dcur + min(ew + 32 * R, w1) > m) {
+                if (lane == 0) atomicOr(err, kErrBounds);
+                return;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int32_t e = ew + 32 * r + (int32_t)lane;
+                ok[r] = e < w1;
+                vv[r] = ok[r] ? ld_edge<false>(g.col + (dcur + e)) : 0;
+            }
+            ew += 32 * R;
+            if (s_next == ew) kcur += 1;
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ok[r] = false;
+                vv[r] = 0;
+                if (ew >= w1) continue;  // warp-uniform
+                if (kcur >= kb + 32) {
+                    kb += 32;
+                    s0 = s1;
+                    d0 = d1;
+                    const int32_t j1 = kb + 32 + (int32_t)lane;
+                    s1 = INT32_MAX;
+                    d1 = 0;
+                    if (j1 < ihiK) { s1 = ld_list<COH>(in.scan + j1); d1 = ld_list<COH>(in.beg + j1) - s1; }
+                }
+                const int32_t p0 = s0 - ew, p1 = s1 - ew;  // entries starting after ew have p > 0
+                const uint32_t bits = ((p0 > 0 && p0 < 32) ? (1u << p0) : 0u) | ((p1 > 0 && p1 < 32) ? (1u << p1) : 0u);
+                const uint32_t starts = __reduce_or_sync(kFull, bits);
+                const int32_t pe = kcur - kb + __popc(starts & upto);  // window position of my entry
+                const int32_t x0 = __shfl_sync(kFull, d0, pe & 31);
+                const int32_t x1 = __shfl_sync(kFull, d1, pe & 31);
+                const int32_t e = ew + (int32_t)lane;
+                const int32_t eidx = (pe < 32 ? x0 : x1) + e;
+                if (e < w1) {
+                    if ((uint32_t)eidx >= (uint32_t)m) {
+                        atomicOr(err, kErrBounds);
+                    } else {
+                        ok[r] = true;
+                        vv[r] = ld_edge<false>(g.col + eidx);
+                    }
+                }
+                // the entry holding the next step's first edge
+                kcur += __popc(starts) + (__ballot_sync(kFull, p0 == 32 || p1 == 32) != 0u ? 1 : 0);
+                ew += 32;
+            }
+        }
+        relax_bfs_lean<R, COH>(ok, vv, g.off, bitmap, status, level, wb, ws, cnt, o);
     }
 }
 
@@ -473,8 +608,8 @@ __device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList
 // R-MAT scale 24), and slower still with that loop at 64-bit width.
 template <bool SSSP, int STEPS, bool COH>
 __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
-                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
-                                             uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
+                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
+                                             uint32_t *status, uint32_t level, uint32_t *err,
                                              WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
     const int64_t q = T / kTileGrain;
     const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
@@ -558,7 +693,7 @@ __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList
                 }
                 if ((LB_WD_PREFETCH & 1) && !SSSP && lane == 0 && rend - ew > 32 * R)
                     bulk_prefetch_l2(g.col + (rbase + ew + 32 * R), g.col + (rbase + rend), g.col + g.m);
-                if (SSSP) rdu = ld_mut<COH>(epoch + ucur) == stamp ? kInf : ld_mut<COH>(status + ucur);
+                if (SSSP) rdu = is_queued<COH>(qcur, ucur) ? kInf : ld_mut<COH>(status + ucur);
             }
         }
         if (rend >= 0) {
@@ -634,7 +769,7 @@ __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList
                         vv[st] = ld_edge<SSSP>(g.col + eidx);
                         if (SSSP) {
                             ww[st] = ld_edge<SSSP>(g.w + eidx);
-                            dd[st] = ld_mut<COH>(epoch + u_l) == stamp ? kInf : ld_mut<COH>(status + u_l);
+                            dd[st] = is_queued<COH>(qcur, u_l) ? kInf : ld_mut<COH>(status + u_l);
                         }
                     }
                 }
@@ -642,8 +777,8 @@ __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList
             ew += 32 * R;
         }
         if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
-        relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, epoch, status, level, stamp,
-                                                         err, wb, ws, cnt, o);
+        relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, qcur, status, level, err, wb,
+                                                         ws, cnt, o);
     }
 }
 
@@ -652,25 +787,27 @@ __device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList
 // the read-only / L1 paths.
 template <bool SSSP, int STEPS, bool COH>
 __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
-                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *epoch,
-                                             uint32_t *status, uint32_t level, uint32_t stamp, uint32_t *err,
+                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
+                                             uint32_t *status, uint32_t level, uint32_t *err,
                                              WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
-    if constexpr (!SSSP && LB_WD_IDX32)
-        wd_walk_tile32<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, epoch, status, level, stamp, err, wb, ws,
+    if constexpr (!SSSP && LB_BFS_WALK2)
+        wd_walk_bfs<STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, status, level, err, wb, ws, cnt, o);
+    else if constexpr (!SSSP && LB_WD_IDX32)
+        wd_walk_tile32<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, qcur, status, level, err, wb, ws,
                                          cnt, o);
     else
-        wd_walk_tile64<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, epoch, status, level, stamp, err, wb, ws,
+        wd_walk_tile64<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, qcur, status, level, err, wb, ws,
                                          cnt, o);
 }
 
 template <bool SSSP, int STEPS>
 __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt, int64_t E,
                                         WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
-                                        uint32_t *status, uint32_t level, uint32_t stamp) {
+                                        uint32_t *status, uint32_t level, uint32_t *qcur) {
     const int64_t T = iteration_tile(E, gridDim.x, p.tile);
     const int64_t ntiles = (E + T - 1) / T;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-        wd_walk_tile<SSSP, STEPS, false>(p.g, in, in_cnt, E, T, t, p.bitmap, p.epoch, status, level, stamp,
+        wd_walk_tile<SSSP, STEPS, false>(p.g, in, in_cnt, E, T, t, p.bitmap, qcur, status, level,
                                          &ctl->error, wb, ws, cnt, o);
 }
 
@@ -683,7 +820,8 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     const int64_t in_cnt = ctl->in_cnt;
     const int64_t E = (int64_t)ctl->in_edges;
     const uint32_t level = ctl->level;
-    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+    if (SSSP) clear_next_queued(p.bitmap, p.bm_words, level);
     uint32_t *status = ctl->status;
     const NodeList in = p.lists[par];
     FlushOut o;
@@ -698,7 +836,7 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     o.pushes = &ctl->pushes;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
-    wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, stamp);
+    wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, qcur);
 #if LB_BLOCK_FLUSH
     wflush_block<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
 #else
@@ -721,7 +859,8 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
     const uint32_t par = ctl->par;
     const int64_t in_cnt = ctl->in_cnt;
     const uint32_t level = ctl->level;
-    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+    if (SSSP) clear_next_queued(p.bitmap, p.bm_words, level);
     uint32_t *status = ctl->status;
     const int32_t *in = p.elist[par];
     FlushOut o;
@@ -760,12 +899,12 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
                 vv[it] = __ldg(p.g.col + e);
                 if (SSSP) {
                     ww[it] = __ldg(p.g.w + e);
-                    dd[it] = sssp_source_dist(status, p.epoch, __ldg(p.coo_src + e), stamp);
+                    dd[it] = sssp_source_dist(status, qcur, __ldg(p.coo_src + e));
                 }
             }
         }
         relax_items<SSSP, ITEMS, CHUNK ? kOutEdges : kOutEdgesPerEdge, false>(
-            ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status, level, stamp, &ctl->error, wb, ws, cnt, o);
+            ok, vv, ww, dd, p.g.off, p.bitmap, qcur, status, level, &ctl->error, wb, ws, cnt, o);
     }
     wflush<kOutEdges, false>(wb, ws, cnt, o);
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, false, p.elist_cap);
@@ -782,9 +921,9 @@ __global__ void __launch_bounds__(kBlock) k_step_ep(StepParams p) {
 // Edges first + lane + k * stride (< last) of one node, relaxed ITEMS per
 // lane at a time from source distance du (the warp and CTA bins of the
 // degree-binned HP step).  first, last and stride are warp-uniform.
-template <bool SSSP, int ITEMS>
+template <bool SSSP, int ITEMS, int OUTK = kOutNode, bool TILED = true>
 __device__ __forceinline__ void serve_range(const StepParams &p, Ctl *ctl, int64_t first, int64_t last, int64_t stride,
-                                            uint32_t du, uint32_t *status, uint32_t level, uint32_t stamp,
+                                            uint32_t du, uint32_t *status, uint32_t level, uint32_t *qcur,
                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
     const uint32_t lane = lane_id();
     for (int64_t e0 = first; e0 < last; e0 += stride * ITEMS) {
@@ -799,9 +938,92 @@ __device__ __forceinline__ void serve_range(const StepParams &p, Ctl *ctl, int64
             ww[it] = (SSSP && ok[it]) ? __ldg(p.g.w + e) : 0u;
             dd[it] = du;
         }
-        if (cnt > kWB - 32 * ITEMS) wflush<kOutNode, true>(wb, ws, cnt, o);
-        relax_items<SSSP, ITEMS, kOutNode, true, false, false>(ok, vv, ww, dd, p.g.off, p.bitmap, p.epoch, status,
-                                                              level, stamp, &ctl->error, wb, ws, cnt, o);
+        if (cnt > kWB - 32 * ITEMS) wflush<OUTK, TILED>(wb, ws, cnt, o);
+        relax_items<SSSP, ITEMS, OUTK, TILED, false, false>(ok, vv, ww, dd, p.g.off, p.bitmap, qcur, status, level,
+                                                           &ctl->error, wb, ws, cnt, o);
+    }
+}
+
+// The degree-binned step (HP's hp_mode 1 and NS's ns_mode 1): every entry
+// of the list is served in this one step at its own granularity -- an
+// entry of at most tmax edges by its own thread, one of at most
+// hp_warp_max edges by its warp (the warp takes its warp-class entries one
+// after another), a larger one by the whole CTA after the block's batches
+// (the CTA bin is a block-local list; when it is full the warp serves the
+// entry instead).  OUTK / TILED: what the pushes write (nodes with tile
+// starts for HP, granules for NS).  Every thread of the block calls it.
+template <bool SSSP, int ITEMS, int OUTK, bool TILED>
+__device__ __forceinline__ void binned_step(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt,
+                                            int64_t tmax, uint32_t *status, uint32_t level, uint32_t *qcur,
+                                            WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    constexpr int kBigCap = 256;
+    __shared__ int32_t s_big[kBigCap];
+    __shared__ uint32_t s_nbig;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+    const int64_t wmax = p.hp_warp_max;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
+        const int64_t i = base + lane;
+        int64_t cur = 0, len = 0;
+        uint32_t du = 0;
+        int cls = -1;  // -1 nothing to do, 0 thread, 1 warp, 2 CTA
+        if (i < in_cnt) {
+            cur = __ldg(in.beg + i);
+            len = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
+            if (cur < 0 || len < 0 || cur + len > p.g.m) {
+                atomicOr(&ctl->error, kErrBounds);
+            } else {
+                if (SSSP) du = sssp_source_dist(status, qcur, __ldg(in.v + i));
+                if (!SSSP || du != kInf) cls = len <= tmax ? 0 : (len <= wmax ? 1 : 2);
+            }
+        }
+        if (cls == 2) {
+            const uint32_t slot = atomicAdd(&s_nbig, 1u);
+            if (slot < (uint32_t)kBigCap) s_big[slot] = (int32_t)i;
+            else cls = 1;
+        }
+        unsigned wm = __ballot_sync(kFull, cls == 1);
+        while (wm) {
+            const int l = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int64_t c0 = __shfl_sync(kFull, cur, l);
+            const int64_t n0 = __shfl_sync(kFull, len, l);
+            const uint32_t d0 = __shfl_sync(kFull, du, l);
+            serve_range<SSSP, ITEMS, OUTK, TILED>(p, ctl, c0, c0 + n0, 32, d0, status, level, qcur, wb, ws, cnt, o);
+        }
+        int64_t end = cls == 0 ? cur + len : cur;
+        while (__any_sync(kFull, cur < end)) {
+            bool want = false;
+            int32_t v = 0;
+            int64_t vb = 0;
+            uint32_t vd = 0;
+            if (cur < end) {
+                v = __ldg(p.g.col + cur);
+                const bool hit = SSSP ? sssp_relax(status, qcur, v, du, __ldg(p.g.w + cur), ctl)
+                                      : bfs_claim(p.bitmap, status, v, level + 1);
+                if (hit) {
+                    vb = __ldg(p.g.off + v);
+                    vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
+                    want = vd > 0;
+                }
+                ++cur;
+            }
+            wpush(wb, cnt, want, v, vb, vd);
+            if (cnt > kWB - 32) wflush<OUTK, TILED>(wb, ws, cnt, o);
+        }
+    }
+    __syncthreads();
+    const uint32_t nbig = s_nbig < (uint32_t)kBigCap ? s_nbig : (uint32_t)kBigCap;
+    for (uint32_t k = 0; k < nbig; ++k) {
+        const int64_t i = s_big[k];
+        const int64_t c0 = __ldg(in.beg + i);
+        const int64_t n0 = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
+        const uint32_t d0 = SSSP ? sssp_source_dist(status, qcur, __ldg(in.v + i)) : 0u;
+        // warp w takes the 32-edge stripes w, w + 8, w + 16, ... of the entry
+        serve_range<SSSP, ITEMS, OUTK, TILED>(p, ctl, c0 + 32 * (int64_t)warp, c0 + n0, kBlock, d0, status, level,
+                                              qcur, wb, ws, cnt, o);
     }
 }
 
@@ -821,6 +1043,11 @@ __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
     const int64_t thr = p.hp_threshold;
     if (kind == 1u && sub_cnt > 0) {
         const uint32_t so = ctl->hp_from == kHpFromSuper ? 0u : (ctl->sub_in ^ 1u);
+        const bool sub_next = !(thr > 0 && sub_cnt < thr);
+        ctl->hp_lvl += 1;
+        // a list within the first hp_depth of the chain gets its own MDT
+        // (k_hp_mdt, before the next sub-iteration); later ones keep it
+        if (p.hp_depth > 1 && ctl->hp_lvl < (uint32_t)p.hp_depth && sub_next) ctl->hp_mdt_pending = 1;
         p.subs[so].scan[sub_cnt] = (int32_t)sub_edges;
         ctl->hp_from = kHpFromSub;
         ctl->sub_in = so;
@@ -844,10 +1071,49 @@ __device__ __forceinline__ void finish_hp_step(const StepParams &p, Ctl *ctl) {
         ctl->level += 1;
         ctl->hp_from = kHpFromSuper;
         ctl->hp_sub = 0;
+        ctl->hp_mdt = (uint32_t)p.mdt;
+        ctl->hp_lvl = 0;
+        ctl->hp_mdt_pending = 0;
+        ctl->sub_maxdeg = 0ull;
         ctl->hp_kind = (thr > 0 && cnt < thr) ? 2u : (p.hp_mode == 1 ? 3u : 1u);
         set_loop(p, ctl, cnt > 0);
     }
     __threadfence();
+}
+
+// ---------------------------------------------------------------------------
+// Node splitting with the granules served at three granularities (ns_mode
+// 1): the list holds the paper's granules (ceil(d / MDT) runs of at most MDT
+// edges per split node, Sec. III-B), and each granule goes to a thread, a
+// warp or the whole CTA by its length, as in the degree-binned HP step.
+template <bool SSSP, int ITEMS>
+__global__ void __launch_bounds__(kBlock) k_step_ns_binned(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const uint32_t par = ctl->par;
+    const int64_t in_cnt = ctl->in_cnt;
+    const uint32_t level = ctl->level;
+    uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+    if (SSSP) clear_next_queued(p.bitmap, p.bm_words, level);
+    uint32_t *status = ctl->status;
+    FlushOut o;
+    o.list = p.lists[par ^ 1u];
+    o.elist = nullptr;
+    o.pack = &ctl->out_pack;
+    o.cap = p.list_cap;
+    o.tile_cap = p.tile_cap;
+    o.tile = (int32_t)kTileGrain;
+    o.mdt = p.mdt;
+    o.err = &ctl->error;
+    o.pushes = &ctl->pushes;
+    o.child_first = nullptr;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t cnt = 0;
+    binned_step<SSSP, ITEMS, kOutGranule, false>(p, ctl, p.lists[par], in_cnt, p.thread_max, status, level, qcur,
+                                                 s_wb[warp], s_ws[warp], cnt, o);
+    wflush<kOutGranule, false>(s_wb[warp], s_ws[warp], cnt, o);
+    if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }
 
 template <bool SSSP, int ITEMS>
@@ -860,7 +1126,8 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     const int64_t in_cnt = ctl->in_cnt;
     const int64_t E = (int64_t)ctl->in_edges;
     const uint32_t level = ctl->level;
-    const uint32_t stamp = ctl->epoch_base + level;
+    uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+    if (SSSP) clear_next_queued(p.bitmap, p.bm_words, level);
     const uint32_t kind = ctl->hp_kind;
     const uint32_t from = ctl->hp_from;
     const uint32_t sub_in = ctl->sub_in;
@@ -885,88 +1152,15 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
     WarpScratch &ws = s_ws[warp];
     uint32_t cnt = 0, scnt = 0;
     if (kind == 2u) {
-        wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, stamp);
+        wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, wb, ws, cnt, osup, status, level, qcur);
     } else if (kind == 3u) {
-        // Degree-binned step (hp_mode 1): the list's nodes are binned by
-        // degree into sub-worklists and all of them are served in this one
-        // step -- a node of at most min(MDT, 32) edges by its own thread, one of at
-        // most hp_warp_max edges by its warp (the warp takes its class-1
-        // nodes one after another), a larger one by the whole CTA after the
-        // block's batches (the CTA bin is a block-local list; when it is full
-        // the warp serves the node instead).
-        constexpr int kBigCap = 256;
-        __shared__ int32_t s_big[kBigCap];
-        __shared__ uint32_t s_nbig;
-        if (threadIdx.x == 0) s_nbig = 0;
-        __syncthreads();
-        // a thread serves at most 32 edges (fewer when MDT is smaller): on a
-        // skewed graph the histogram MDT runs into the thousands
-        const int64_t tmax = p.mdt < 32 ? (int64_t)p.mdt : 32;
-        const int64_t wmax = p.hp_warp_max;
-        const int64_t stride = (int64_t)gridDim.x * kBlock;
-        for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
-            const int64_t i = base + lane;
-            int64_t cur = 0, len = 0;
-            uint32_t du = 0;
-            int cls = -1;  // -1 nothing to do, 0 thread, 1 warp, 2 CTA
-            if (i < in_cnt) {
-                cur = __ldg(in.beg + i);
-                len = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
-                if (cur < 0 || len < 0 || cur + len > p.g.m) {
-                    atomicOr(&ctl->error, kErrBounds);
-                } else {
-                    if (SSSP) du = sssp_source_dist(status, p.epoch, __ldg(in.v + i), stamp);
-                    if (!SSSP || du != kInf) cls = len <= tmax ? 0 : (len <= wmax ? 1 : 2);
-                }
-            }
-            if (cls == 2) {
-                const uint32_t slot = atomicAdd(&s_nbig, 1u);
-                if (slot < (uint32_t)kBigCap) s_big[slot] = (int32_t)i;
-                else cls = 1;
-            }
-            unsigned wm = __ballot_sync(kFull, cls == 1);
-            while (wm) {
-                const int l = __ffs(wm) - 1;
-                wm &= wm - 1;
-                const int64_t c0 = __shfl_sync(kFull, cur, l);
-                const int64_t n0 = __shfl_sync(kFull, len, l);
-                const uint32_t d0 = __shfl_sync(kFull, du, l);
-                serve_range<SSSP, ITEMS>(p, ctl, c0, c0 + n0, 32, d0, status, level, stamp, wb, ws, cnt, osup);
-            }
-            int64_t end = cls == 0 ? cur + len : cur;
-            while (__any_sync(kFull, cur < end)) {
-                bool want = false;
-                int32_t v = 0;
-                int64_t vb = 0;
-                uint32_t vd = 0;
-                if (cur < end) {
-                    v = __ldg(p.g.col + cur);
-                    const bool hit = SSSP ? sssp_relax(status, p.epoch, v, du, __ldg(p.g.w + cur), stamp, ctl)
-                                          : bfs_claim(p.bitmap, status, v, level + 1);
-                    if (hit) {
-                        vb = __ldg(p.g.off + v);
-                        vd = (uint32_t)(__ldg(p.g.off + v + 1) - vb);
-                        want = vd > 0;
-                    }
-                    ++cur;
-                }
-                wpush(wb, cnt, want, v, vb, vd);
-                if (cnt > kWB - 32) wflush<kOutNode, true>(wb, ws, cnt, osup);
-            }
-        }
-        __syncthreads();
-        const uint32_t nbig = s_nbig < (uint32_t)kBigCap ? s_nbig : (uint32_t)kBigCap;
-        for (uint32_t k = 0; k < nbig; ++k) {
-            const int64_t i = s_big[k];
-            const int64_t c0 = __ldg(in.beg + i);
-            const int64_t n0 = __ldg(in.scan + i + 1) - __ldg(in.scan + i);
-            const uint32_t d0 = SSSP ? sssp_source_dist(status, p.epoch, __ldg(in.v + i), stamp) : 0u;
-            // warp w takes the 32-edge stripes w, w + 8, w + 16, ... of the node
-            serve_range<SSSP, ITEMS>(p, ctl, c0 + 32 * (int64_t)warp, c0 + n0, kBlock, d0, status, level, stamp, wb,
-                                     ws, cnt, osup);
-        }
+        // a thread serves at most min(MDT, thread_max) edges: on a skewed
+        // graph the histogram MDT runs into the thousands
+        const int64_t tmax = p.mdt < p.thread_max ? (int64_t)p.mdt : (int64_t)p.thread_max;
+        binned_step<SSSP, ITEMS, kOutNode, true>(p, ctl, in, in_cnt, tmax, status, level, qcur, wb, ws, cnt, osup);
     } else {
-        const int64_t mdt = p.mdt;
+        const int64_t mdt = (int64_t)ctl->hp_mdt;
+        const bool track = p.hp_depth > 1;  // the sub-list's largest remaining degree, for k_hp_mdt
         const int64_t stride = (int64_t)gridDim.x * kBlock;
         for (int64_t base = (int64_t)blockIdx.x * kBlock + warp * 32; base < in_cnt; base += stride) {
             const int64_t i = base + lane;
@@ -984,11 +1178,15 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
                     end = cur + take;
                     rest = len - take;
                     u = __ldg(in.v + i);
-                    if (SSSP) du = sssp_source_dist(status, p.epoch, u, stamp);
+                    if (SSSP) du = sssp_source_dist(status, qcur, u);
                 }
             }
             // an entry skipped as redundant (SSSP, see sssp_source_dist) leaves no remainder
             const bool keep = rest > 0 && (!SSSP || du != kInf);
+            if (track) {
+                const uint32_t mx = __reduce_max_sync(kFull, keep ? (uint32_t)rest : 0u);
+                if (lane == 0 && mx > 0) atomicMax(&ctl->sub_maxdeg, (unsigned long long)mx);
+            }
             if (SSSP && du == kInf) end = cur;
             wpush(sb, scnt, keep, u, end, (uint32_t)rest);
             if (scnt > kWB - 32) wflush<kOutNode, true>(sb, ws, scnt, osub);
@@ -999,7 +1197,7 @@ __global__ void __launch_bounds__(kBlock) k_step_hp(StepParams p) {
                 uint32_t vd = 0;
                 if (cur < end) {
                     v = __ldg(p.g.col + cur);
-                    const bool hit = SSSP ? sssp_relax(status, p.epoch, v, du, __ldg(p.g.w + cur), stamp, ctl)
+                    const bool hit = SSSP ? sssp_relax(status, qcur, v, du, __ldg(p.g.w + cur), ctl)
                                           : bfs_claim(p.bitmap, status, v, level + 1);
                     if (hit) {
                         vb = __ldg(p.g.off + v);

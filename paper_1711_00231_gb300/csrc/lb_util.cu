@@ -12,7 +12,8 @@ namespace lbk {
 cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, cudaStream_t st) {
     switch (strategy) {
         case LB_BS: return launch_step_entry(sssp, false, p, grid, st);
-        case LB_NS: return launch_step_entry(sssp, true, p, grid, st);
+        case LB_NS: return p.ns_mode == 1 ? launch_step_ns_binned(sssp, p, grid, st)
+                                          : launch_step_entry(sssp, true, p, grid, st);
         case LB_NS_PHYS: return launch_step_phys(sssp, p, grid, st);
         case LB_WD: return launch_step_wd(sssp, p, grid, st);
         case LB_EP: return launch_step_ep(sssp, true, p, grid, st);
@@ -22,10 +23,10 @@ cudaError_t launch_step(int strategy, bool sssp, const StepParams &p, int grid, 
     }
 }
 
-int step_blocks_per_sm(int strategy, bool sssp) {
+int step_blocks_per_sm(int strategy, bool sssp, int ns_mode) {
     switch (strategy) {
         case LB_BS: return occupancy_step_entry(sssp, false);
-        case LB_NS: return occupancy_step_entry(sssp, true);
+        case LB_NS: return ns_mode == 1 ? occupancy_step_ns_binned(sssp) : occupancy_step_entry(sssp, true);
         case LB_NS_PHYS: return occupancy_step_phys(sssp);
         case LB_WD: return occupancy_step_wd(sssp);
         case LB_EP: return occupancy_step_ep(sssp, true);
@@ -64,16 +65,13 @@ __global__ void k_prepare(StepParams p, int32_t src, uint32_t *status, int kind,
     c->hp_sub = 0;
     c->sub_in = 0;
     c->hp_kind = (p.hp_threshold > 0 && (int64_t)c->in_cnt < p.hp_threshold) ? 2u : (p.hp_mode == 1 ? 3u : 1u);
+    c->hp_mdt = (uint32_t)p.mdt;
+    c->hp_lvl = 0;
+    c->hp_mdt_pending = 0;
+    c->sub_maxdeg = 0ull;
     c->blocks_done = 0;
     c->active = 1;
     c->error = 0;
-    if (c->epoch_next == 0u || c->epoch_next > 0xF0000000u) {
-        c->epoch_reset = 1;
-        c->epoch_base = 1;
-    } else {
-        c->epoch_reset = 0;
-        c->epoch_base = c->epoch_next;
-    }
     c->max_levels = max_levels;
     c->max_steps = max_steps;
     c->t_start = global_ns();
@@ -92,15 +90,15 @@ __global__ void k_init(StepParams p) {
     const int64_t n = p.g.n;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const bool reset_epoch = c->epoch_reset != 0;
-    for (int64_t i = tid; i < n; i += stride) {
-        status[i] = i == src ? 0u : kInf;
-        if (sssp && reset_epoch) p.epoch[i] = 0u;
-    }
+    for (int64_t i = tid; i < n; i += stride) status[i] = i == src ? 0u : kInf;
     if (!sssp) {
+        // BFS: the visited bits (first half), the source already visited
         const int64_t words = (n + 31) / 32;
         for (int64_t wd = tid; wd < words; wd += stride)
             p.bitmap[wd] = wd == (src >> 5) ? (1u << (src & 31)) : 0u;
+    } else {
+        // SSSP: both queued halves start empty
+        for (int64_t wd = tid; wd < 2 * p.bm_words; wd += stride) p.bitmap[wd] = 0u;
     }
     const int64_t beg = p.g.off[src];
     const int64_t deg = p.g.off[src + 1] - beg;
@@ -153,6 +151,54 @@ __global__ void k_finish_query(StepParams p) {
             atomicOr(&c->error, kErrOverflow);
             return;
         }
+}
+
+// HP hierarchy depth > 1 (Sec. III-C: a large sub-worklist is partitioned
+// again, the MDT deciding the split): before a sub-iteration whose input
+// sub-list is still within the first hp_depth lists of the super-iteration's
+// chain, that list gets its own MDT -- the histogram heuristic of Sec.
+// III-B applied to the remaining degrees of its entries (bins of equal width
+// over (0, maxRemaining], the tallest, smallest on a tie; MDT = max(1,
+// floor(binIndex * maxRemaining / bins))).  A no-op launch otherwise.
+__global__ void k_hp_mdt(StepParams p) {
+    Ctl *c = p.ctl;
+    if (!c->hp_mdt_pending) return;  // uniform
+    const int bins = p.hist_bins;
+    const int64_t maxd = (int64_t)c->sub_maxdeg;
+    const int64_t cnt = c->in_cnt;
+    const NodeList in = p.subs[c->sub_in];
+    __shared__ uint32_t sh[kHistMax];
+    for (int k = threadIdx.x; k < bins; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (maxd > 0)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+            const int64_t d = (int64_t)in.scan[i + 1] - in.scan[i];
+            if (d <= 0 || d > maxd) continue;
+            const int64_t k = (d * bins + maxd - 1) / maxd;  // 1-based bin
+            atomicAdd(&sh[k - 1], 1u);
+        }
+    __syncthreads();
+    for (int k = threadIdx.x; k < bins; k += blockDim.x)
+        if (sh[k]) atomicAdd(&c->hp_hist[k], sh[k]);
+    if (block_is_last(c) && threadIdx.x == 0) {
+        __threadfence();
+        int best = 0;
+        for (int k = 1; k < bins; ++k)
+            if (__ldcg(&c->hp_hist[k]) > __ldcg(&c->hp_hist[best])) best = k;
+        const int64_t mdt = maxd > 0 ? ((int64_t)(best + 1) * maxd) / bins : 1;
+        c->hp_mdt = (uint32_t)(mdt < 1 ? 1 : mdt);
+        for (int k = 0; k < bins; ++k) c->hp_hist[k] = 0;
+        c->sub_maxdeg = 0ull;
+        c->hp_mdt_pending = 0;
+        c->blocks_done = 0;
+        __threadfence();
+    }
+}
+
+cudaError_t launch_hp_mdt(const StepParams &p, int grid, cudaStream_t st) {
+    k_hp_mdt<<<grid, kBlock, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prepare(const StepParams &p, int32_t src, uint32_t *status, int kind, uint32_t max_levels,

@@ -37,7 +37,8 @@ class LbError(RuntimeError):
 class lb_options(ctypes.Structure):
     _fields_ = [("hist_bins", ctypes.c_int32), ("mdt_override", ctypes.c_int32), ("hp_threshold", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("wd_tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("hp_mode", ctypes.c_int32), ("hp_warp_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("hp_mode", ctypes.c_int32), ("hp_warp_max", ctypes.c_int32), ("ns_mode", ctypes.c_int32),
+                ("thread_max", ctypes.c_int32), ("hp_depth", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class lb_mem_stats(ctypes.Structure):
@@ -506,7 +507,8 @@ class Graph:
         return lb_mdt(self.h, bins)
 
     def autotune(self, kind: str, strategy, srcs):
-        return lb_autotune(self.h, LB_KIND_BFS if kind == "bfs" else LB_KIND_SSSP, strategy, srcs)
+        """kind: "bfs", "sssp" or "both" (one BFS and one SSSP per source)."""
+        return lb_autotune(self.h, {"bfs": LB_KIND_BFS, "sssp": LB_KIND_SSSP, "both": 2}[kind], strategy, srcs)
 
     def release(self):
         lb_release_workspaces(self.h)

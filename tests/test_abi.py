@@ -48,7 +48,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lb_options), sizeof(lb_mem_stats), sizeof(lb_query_stats), sizeof(lb_step_record));
   printf("%zu %zu %zu %zu\n", offsetof(lb_query_stats, status), offsetof(lb_query_stats, device_ms), offsetof(lb_mem_stats, ns_split), offsetof(lb_step_record, t_ns));
   printf("%zu %zu %zu %zu\n", sizeof(lb_server_state_t), sizeof(lb_slot_state_t), offsetof(lb_server_state_t, slot), offsetof(lb_slot_state_t, ticket));
-  printf("%zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max),
+         offsetof(lb_options, ns_mode), offsetof(lb_options, thread_max), offsetof(lb_options, hp_depth),
+         sizeof(lb_options));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -62,7 +64,9 @@ int main(void) {
                     lb.lb_step_record.t_ns.offset]
     assert [int(x) for x in c.split()] == [ctypes.sizeof(lb.lb_server_state_t), ctypes.sizeof(lb.lb_slot_state_t),
                                            lb.lb_server_state_t.slot.offset, lb.lb_slot_state_t.ticket.offset]
-    assert [int(x) for x in d.split()] == [lb.lb_options.hp_mode.offset, lb.lb_options.hp_warp_max.offset]
+    assert [int(x) for x in d.split()] == [lb.lb_options.hp_mode.offset, lb.lb_options.hp_warp_max.offset,
+                                           lb.lb_options.ns_mode.offset, lb.lb_options.thread_max.offset,
+                                           lb.lb_options.hp_depth.offset, ctypes.sizeof(lb.lb_options)]
 
 
 def test_version_and_error_string():

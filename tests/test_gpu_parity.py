@@ -104,12 +104,28 @@ def test_hp_degree_binned_matches_oracle(opts):
             G.close()
 
 
+@pytest.mark.parametrize("opts", [dict(ns_mode=1), dict(ns_mode=1, thread_max=1), dict(ns_mode=1, hp_warp_max=32),
+                                  dict(ns_mode=1, mdt_override=1), dict(ns_mode=1, mdt_override=5000, thread_max=64)])
+def test_ns_binned_granules_match_oracle(opts):
+    # NS with its granules served by a thread (<= thread_max edges), a warp
+    # (<= hp_warp_max) or the whole CTA; thread_max = 1 sends almost every
+    # granule to a warp, hp_warp_max = 32 overflows the per-block CTA bin,
+    # mdt_override = 1 makes every edge its own granule, 5000 leaves hubs whole
+    graphs = [(gg.rmat(14, 16, seed=1), [0, 17]), (gg.rmat(16, 16, seed=7), None),
+              (gg.grid(64, 48, seed=3), [0, 1000]), (gg.erdos_renyi(3000, 12000, seed=4), [5])]
+    for g, srcs in graphs:
+        if srcs is None:
+            srcs = [gg.max_degree_vertex(g)]
+        run_all(g, srcs, strategies=["NS"], options=opts)
+
+
 def test_option_validation():
     g = gg.rmat(10, 8, seed=1)
     G = lb.Graph.from_csr(g)
     try:
         for bad in [dict(hp_mode=2), dict(hp_warp_max=16), dict(wd_tile=300), dict(wd_tile=65536), dict(loop_mode=3),
-                    dict(hist_bins=5000), dict(ctas_per_sm=40)]:
+                    dict(hist_bins=5000), dict(ctas_per_sm=40), dict(ns_mode=2), dict(thread_max=2000),
+                    dict(thread_max=-1), dict(hp_depth=9), dict(hp_depth=-2)]:
             with pytest.raises(lb.LbError):
                 G.set_options(**bad)
         G.set_options(hp_mode=1, hp_warp_max=64)
@@ -202,8 +218,11 @@ def test_erdos_renyi_er20_shape():
 
 
 # every strategy and form, as (strategy, options) pairs: the paper's HP
-# sub-iterations and the degree-binned HP step are both run
-ALL_FORMS = [(s, dict(hp_mode=0)) for s in STRATS] + [("HP", dict(hp_mode=1))]
+# sub-iterations and the degree-binned HP step, the paper's NS (thread per
+# granule) and its binned form, HP with a two-level hierarchy
+ALL_FORMS = ([(s, dict(hp_mode=0, ns_mode=0, hp_depth=1)) for s in STRATS] +
+             [("HP", dict(hp_mode=1, ns_mode=0, hp_depth=1)), ("NS", dict(hp_mode=0, ns_mode=1, hp_depth=1)),
+              ("HP", dict(hp_mode=0, ns_mode=0, hp_depth=2))])
 
 
 def run_forms(G, g, src, ref_lev, ref_dist, forms=ALL_FORMS):
@@ -218,7 +237,7 @@ def run_forms(G, g, src, ref_lev, ref_dist, forms=ALL_FORMS):
             d, rc = G.sssp(src, s)
             assert rc == lb.LB_OK, (s, opts, rc)
             assert np.array_equal(d, ref_dist), f"SSSP {s} {opts} src={src}: {np.flatnonzero(d != ref_dist)[:10]}"
-    G.set_options(hp_mode=0)
+    G.set_options(hp_mode=0, ns_mode=0, hp_depth=1)
 
 
 @pytest.fixture(scope="module")
@@ -232,6 +251,24 @@ def rmat24():
     # R-MAT scale 24, edge factor 32, a/b/c/d = .57/.19/.19/.05, weights
     # U[1,255], seed 1 (the benchmark's graph)
     return gg.rmat(24, 32, seed=1)
+
+
+def test_erdos_renyi_er23_shape():
+    # ER23 of Table II: 8.39M nodes, 33.55M edges (uniform random edges), every
+    # strategy and form from two sources against the oracle, and the device
+    # histogram MDT against the oracle's.  (Table II prints MDT 3 at maximum
+    # degree 10 for the paper's ER23; this stand-in draws G(n, m) edges, whose
+    # Poisson tail reaches degree 20, and its histogram MDT is 4.)
+    g = gg.erdos_renyi(1 << 23, 33554432, seed=1)
+    G = lb.Graph.from_csr(g)
+    try:
+        for src in gg.pick_sources(g, 2, seed=1).tolist():
+            ref_lev, _ = oracle.bfs(g, src)
+            ref, _ = oracle.dijkstra(g, src)
+            run_forms(G, g, src, ref_lev, ref)
+        assert G.mdt(10) == oracle.mdt(g.offsets, 10)[:3]
+    finally:
+        G.close()
 
 
 def test_grid4096_sssp_from_corner(grid4096):
@@ -430,19 +467,56 @@ def test_hp_trace_matches_paper_example():
         G.close()
 
 
-def test_hp_trace_matches_oracle_on_rmat():
+def test_hp_depth_trace_matches_worked_examples():
+    # HP with a two-level hierarchy on the golden hand-worked cases: the
+    # paper's two-node figure (edges 6, 4, 2) and two hubs behind ten light
+    # nodes (the sub-list's own MDT 1078 finishes them in 3 sub-iterations)
+    import json
+    import os
+    gd = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hp_depth_example.json")))
+    for case in gd["cases"]:
+        degs = case["degrees"]
+        # 0 -> the frontier nodes 1..F, each with its own fresh leaves
+        src, dst, nxt = list(range(1, len(degs) + 1)), [], len(degs) + 1
+        src = [0] * len(degs)
+        dst = list(range(1, len(degs) + 1))
+        for i, d in enumerate(degs):
+            src += [i + 1] * d
+            dst += list(range(nxt, nxt + d))
+            nxt += d
+        g = gg.from_edges(nxt, src, dst, np.ones(len(src), int))
+        G = lb.Graph.from_csr(g)
+        try:
+            G.set_options(mdt_override=case["mdt"], hp_threshold=-1, hp_depth=case["depth"], hist_bins=gd["bins"])
+            for kind in ("bfs", "sssp"):
+                if kind == "bfs":
+                    assert np.array_equal(G.bfs(0, "HP"), oracle.bfs(g, 0)[0])
+                else:
+                    d, rc = G.sssp(0, "HP")
+                    assert rc == lb.LB_OK and np.array_equal(d, oracle.dijkstra(g, 0)[0])
+                tr = G.trace()
+                lvl1 = tr[tr["level"] == 1]
+                assert lvl1["list_size"].tolist() == case["list_sizes"], (case["name"], kind)
+                assert lvl1["edges"].tolist() == case["edges"], (case["name"], kind)
+        finally:
+            G.close()
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_hp_trace_matches_oracle_on_rmat(depth):
     g = gg.rmat(14, 16, seed=2)
     G = lb.Graph.from_csr(g)
     try:
         mdt = oracle.mdt(g.offsets, 10)[0]
         for thr in (-1, 64, 1024):
-            G.set_options(hp_threshold=thr)
+            G.set_options(hp_threshold=thr, hp_depth=depth)
             lev = G.bfs(0, "HP")
+            assert np.array_equal(lev, oracle.bfs(g, 0)[0])
             tr = G.trace()
             deg = g.degrees()
             for L in np.unique(tr["level"]):
                 front = np.flatnonzero((lev == L) & (deg > 0))
-                ls, ed, md = oracle.hp_schedule(deg[front], mdt, threshold=max(thr, 0))
+                ls, ed, md = oracle.hp_schedule(deg[front], mdt, threshold=max(thr, 0), depth=depth)
                 rows = tr[tr["level"] == L]
                 assert rows["list_size"].tolist() == ls.tolist(), (thr, L)
                 assert rows["edges"].tolist() == ed.tolist(), (thr, L)
@@ -452,17 +526,19 @@ def test_hp_trace_matches_oracle_on_rmat():
 
 
 def test_ns_granules_match_paper_example():
-    # node 8 with 7 out-edges at MDT 4 is served as two granules of 4 and 3
+    # node 8 with 7 out-edges at MDT 4 is served as two granules of 4 and 3,
+    # in the paper's form (a thread per granule) and in the binned form
     g = _two_node_frontier_graph(5, 7)
     G = lb.Graph.from_csr(g)
     try:
-        G.set_options(mdt_override=4)
-        G.bfs(0, "NS")
-        tr = G.trace()
-        lvl1 = tr[tr["level"] == 1]
-        runs = [len(oracle.ns_chunks(5, 4)), len(oracle.ns_chunks(7, 4))]
-        assert runs == [2, 2]
-        assert lvl1["list_size"].tolist() == [sum(runs)] and lvl1["edges"].tolist() == [12]
+        for ns_mode in (1, 0):
+            G.set_options(mdt_override=4, ns_mode=ns_mode)
+            assert np.array_equal(G.bfs(0, "NS"), oracle.bfs(g, 0)[0])
+            tr = G.trace()
+            lvl1 = tr[tr["level"] == 1]
+            runs = [len(oracle.ns_chunks(5, 4)), len(oracle.ns_chunks(7, 4))]
+            assert runs == [2, 2]
+            assert lvl1["list_size"].tolist() == [sum(runs)] and lvl1["edges"].tolist() == [12]
         rep = G.mem_report("NS")
         assert rep["mdt"] == 4 and rep["ns_children"] == oracle.ns_split(g.offsets, 4)[0] == 2
     finally:

@@ -255,6 +255,37 @@ def test_hp_worked_example():
     assert len(ls) == 20
 
 
+def test_hp_depth_worked_examples():
+    # hierarchy depth > 1: hand-worked cases of the rule (golden file), the
+    # sub-list MDT re-derived with the pinned graph-MDT function on a CSR
+    # whose degrees are the remaining degrees, and depth 1 = the plain schedule
+    gd = golden("hp_depth_example.json")
+    for case in gd["cases"]:
+        ls, ed, md = oracle.hp_schedule(case["degrees"], case["mdt"], threshold=0, depth=case["depth"],
+                                        bins=gd["bins"])
+        assert ls.tolist() == case["list_sizes"] and ed.tolist() == case["edges"], case["name"]
+        assert (md == 0).all() and ed.sum() == sum(case["degrees"])
+        if "subiterations_at_depth_1" in case:
+            assert len(oracle.hp_schedule(case["degrees"], case["mdt"], threshold=0)[0]) == \
+                case["subiterations_at_depth_1"]
+    rng = np.random.default_rng(11)
+    for trial in range(30):
+        deg = rng.integers(1, 400, int(rng.integers(1, 60)))
+        deg[rng.random(deg.size) < 0.1] = rng.integers(1000, 5000)
+        mdt0 = int(rng.integers(1, 50))
+        plain = oracle.hp_schedule(deg, mdt0, threshold=0)
+        d1 = oracle.hp_schedule(deg, mdt0, threshold=0, depth=1)
+        assert all(np.array_equal(a, b) for a, b in zip(plain, d1))
+        ls, ed, _ = oracle.hp_schedule(deg, mdt0, threshold=0, depth=2)
+        assert ed.sum() == deg.sum()
+        if len(ls) > 1:
+            rem = np.maximum(deg - mdt0, 0)
+            rem = rem[rem > 0]
+            off = np.concatenate([[0], np.cumsum(rem)])
+            mdt1 = oracle.mdt(off, 10)[0]
+            assert ed[1] == np.minimum(rem, mdt1).sum(), trial
+
+
 def test_ns_worked_example():
     gd = golden("ns_example.json")
     runs = oracle.ns_chunks(gd["degree"], gd["mdt"])
