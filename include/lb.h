@@ -120,7 +120,18 @@ typedef struct lb_options {
                               super list uses the graph's MDT); later
                               sub-lists keep the last one (Sec. III-C: "the
                               depth of this hierarchy is tunable") */
-    int32_t reserved[5];
+    int32_t small_edges;   /* WD: while the worklist has at most this many
+                              edges, levels run inside one persistent launch
+                              (one CTA per SM, a grid barrier between levels)
+                              instead of a launch per level: high-diameter
+                              graphs have thousands of such levels.
+                              0..16777216; 0 = off (65536) */
+    int32_t test_barrier_skip; /* test hook, 0 in normal use: 1 makes CTA 1 of
+                              the small-list launch leave before its first
+                              grid barrier, so the other CTAs' bounded waits
+                              run out (2 s) and the query returns
+                              LB_ERR_TIMEOUT with the device still usable */
+    int32_t reserved[3];
 } lb_options;
 
 /* Device bytes by structure (lb_mem_report).  "extra" is everything a
@@ -168,7 +179,9 @@ typedef struct lb_query_stats {
 typedef struct lb_step_record {
     int32_t level;         /* super-iteration (BFS level of the list) */
     int32_t mode;          /* 0 relax, 1 HP sub-iteration, 2 HP WD step,
-                              3 HP degree-binned step (hp_mode 1) */
+                              3 HP degree-binned step (hp_mode 1), 4 WD
+                              level inside the persistent small-list
+                              launch */
     int64_t list_size;     /* entries in the list this step consumed */
     int64_t edges;         /* edges relaxed by this step */
     int64_t t_ns;          /* device time at the end of the step, in ns from
@@ -302,7 +315,12 @@ typedef struct lb_server_options {
                              pending or in flight the next submit / poll
                              relaunches it and they continue where they
                              were (their state is in device memory) */
-    int32_t reserved[7];
+    int32_t policy;       /* tile claiming: 0 = the oldest query in flight
+                             first (its iterations run as if it were alone;
+                             the other queries fill the CTAs it leaves
+                             idle), then round robin over the busy slots;
+                             1 = round robin only (0) */
+    int32_t reserved[6];
 } lb_server_options;
 
 typedef struct lb_server_info_t {

@@ -79,6 +79,10 @@ struct DeviceGuard {
 
 constexpr int kStrategies = 7;
 
+#ifndef LB_SMALL_EDGES_DEFAULT
+#define LB_SMALL_EDGES_DEFAULT 65536
+#endif
+
 constexpr int32_t LB_TUNE_BOTH = 2;  // lb_autotune: time a BFS and an SSSP per source
 
 bool is_ep(int s) { return s == LB_EP || s == LB_EP_NOCHUNK; }
@@ -182,6 +186,7 @@ lb_options default_options() {
     o.ns_mode = 0;
     o.thread_max = 32;
     o.hp_depth = 1;
+    o.small_edges = LB_SMALL_EDGES_DEFAULT;
     o.loop_mode = 0;
     o.wd_tile = 8192;
     o.ctas_per_sm = 0;
@@ -201,7 +206,9 @@ lb_status normalise_options(const lb_options *in, lb_options *out) {
     if (o.ns_mode != 0 && o.ns_mode != 1) return fail(LB_ERR_ARG, "ns_mode must be 0 or 1");
     if (o.thread_max < 1 || o.thread_max > 1024) return fail(LB_ERR_ARG, "thread_max must be in [1, 1024]");
     if (o.hp_depth < 1 || o.hp_depth > 8) return fail(LB_ERR_ARG, "hp_depth must be in [1, 8]");
-    for (int i = 0; i < 5; ++i)
+    if (o.small_edges < 0 || o.small_edges > (1 << 24)) return fail(LB_ERR_ARG, "small_edges must be in [0, 2^24]");
+    if (o.test_barrier_skip != 0 && o.test_barrier_skip != 1) return fail(LB_ERR_ARG, "test_barrier_skip must be 0 or 1");
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return fail(LB_ERR_ARG, "reserved option fields must be 0");
     if (o.wd_tile == 0) o.wd_tile = d.wd_tile;
     if (o.hist_bins < 1 || o.hist_bins > 4096) return fail(LB_ERR_ARG, "hist_bins must be in [1, 4096]");
@@ -407,6 +414,8 @@ StepParams make_params(const lb_graph *g, int s) {
     p.ns_mode = g->opt.ns_mode;
     p.hp_depth = g->opt.hp_depth;
     p.hist_bins = g->opt.hist_bins;
+    p.small_edges = s == LB_WD ? g->opt.small_edges : 0;
+    p.test_barrier_skip = g->opt.test_barrier_skip;
     p.strategy = s;
     p.use_cond = 0;
     return p;
@@ -421,6 +430,9 @@ int step_grid(lb_graph *g, int s, bool sssp) {
     }
     return gr;
 }
+
+// CTAs of the persistent small-list launch (all resident: a cooperative launch).
+int small_grid(const lb_graph *g) { return g->sms * small_ctas_per_sm(); }
 
 // HP with a hierarchy deeper than one list runs k_hp_mdt before every step.
 bool hp_needs_mdt_kernel(const lb_graph *g, int s) { return s == LB_HP && g->opt.hp_depth > 1; }
@@ -459,6 +471,7 @@ lb_status build_exec(lb_graph *g, int s, bool sssp, cudaGraphExec_t *out) {
     if (e == cudaSuccess) {
         cudaError_t le = cudaSuccess;
         if (hp_needs_mdt_kernel(g, s)) le = launch_hp_mdt(p, 2 * g->sms, g->stream);
+        if (le == cudaSuccess && p.small_edges > 0) le = launch_small_levels(sssp, p, small_grid(g), g->stream);
         if (le == cudaSuccess) le = launch_step(s, sssp, p, grid, g->stream);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(g->stream, &captured);
@@ -509,6 +522,7 @@ lb_status run_query(lb_graph *g, int kind, int s, int32_t src, void *out_dev, in
     } else {
         for (;;) {
             if (hp_needs_mdt_kernel(g, s)) LB_CU(launch_hp_mdt(p, 2 * g->sms, st));
+            if (p.small_edges > 0) LB_CU(launch_small_levels(sssp, p, small_grid(g), st));
             LB_CU(launch_step(s, sssp, p, grid, st));
             LB_CU(cudaMemcpyAsync(g->hflag, &g->ctl->active, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             LB_CU(cudaStreamSynchronize(st));

@@ -57,28 +57,6 @@ struct FlushOut {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// L2 prefetch hints: the lines are requested now and no register waits for
-// them, so a warp can have far more of its upcoming edges in flight than it
-// holds loads for.
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// One bulk prefetch (cp.async.bulk.prefetch.L2) of the bytes [p, q) of an
-// array that ends at `limit`: the start is rounded down to 16 bytes and the
-// end rounded up but kept within the array's last whole 16 bytes.  Issued
-// by one thread.
-__device__ __forceinline__ void bulk_prefetch_l2(const void *p, const void *q, const void *limit) {
-    const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
-    uintptr_t b = ((uintptr_t)q + 15) & ~(uintptr_t)15;
-    const uintptr_t lim = (uintptr_t)limit & ~(uintptr_t)15;
-    if (b > lim) b = lim;
-    if (b > a) {
-        const uint32_t bytes = (uint32_t)min((uintptr_t)(b - a), (uintptr_t)(1u << 20));
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
-    }
-}
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -428,6 +406,9 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
     }
 }
 
+#ifndef LB_LEAN_PUSH_SIMPLE
+#define LB_LEAN_PUSH_SIMPLE 0
+#endif
 // BFS relax of R loaded edges per lane with warp-uniform early exits: the
 // visited check for every item, then (only if some lane of the warp found
 // an unvisited vertex) the claims, then (only if some lane won one) the
@@ -468,6 +449,22 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
             vd[r] = (int32_t)__ldg(off + vv[r] + 1) - vb[r];
         }
     }
+#if LB_LEAN_PUSH_SIMPLE
+    // flush whenever a full group might not fit, then push item by item
+    if (cnt > (uint32_t)(kWB - 32 * R)) wflush<kOutNode, true>(wb, ws, cnt, o);
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned b = __ballot_sync(kFull, ((won >> r) & 1u) && vd[r] > 0);
+        if ((b >> lane_id()) & 1u) {
+            const uint32_t s = cnt + __popc(b & lt);
+            wb.v[s] = vv[r];
+            wb.beg[s] = vb[r];
+            wb.deg[s] = (uint32_t)vd[r];
+        }
+        cnt += __popc(b);
+    }
+#else
     unsigned bal[R];
     uint32_t tot = 0;
 #pragma unroll
@@ -488,6 +485,7 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
         }
         cnt += __popc(bal[r]);
     }
+#endif
     __syncwarp();
 }
 

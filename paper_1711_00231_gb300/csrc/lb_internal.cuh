@@ -47,7 +47,7 @@ enum : uint32_t {
 };
 
 // step modes recorded in the trace
-enum : int32_t { kModeRelax = 0, kModeHpSub = 1, kModeHpWd = 2, kModeHpBin = 3 };
+enum : int32_t { kModeRelax = 0, kModeHpSub = 1, kModeHpWd = 2, kModeHpBin = 3, kModeSmall = 4 };
 
 // which list an HP step reads
 enum : uint32_t { kHpFromSuper = 0, kHpFromSub = 1 };
@@ -80,6 +80,11 @@ struct Ctl {
     uint32_t hp_mdt_pending;  // HP: the input sub-list needs its own MDT (k_hp_mdt)
     uint32_t hp_pad;
     unsigned long long sub_maxdeg;  // HP: largest remaining degree pushed to the sub-list
+    unsigned long long small_pack[3];  // small-list levels: output counters, level L uses L % 3
+    uint32_t bar_count;     // small-list levels: CTAs arrived at the grid barrier
+    uint32_t bar_gen;       // small-list levels: barrier generation
+    uint32_t bar_stop;      // small-list levels: the releasing CTA saw the time limit pass
+    uint32_t bar_pad;
     uint32_t sub_in;    // HP: sub list buffer read when hp_from == kHpFromSub
     uint32_t blocks_done;
     uint32_t active;    // loop condition
@@ -139,9 +144,10 @@ struct StepParams {
     int32_t ns_mode;       // 0: thread per granule, 1: binned granules
     int32_t hp_depth;      // HP: lists of a super-iteration's chain with their own MDT
     int32_t hist_bins;     // HistogramBinCount of the MDT heuristic
+    int32_t test_barrier_skip;  // test hook: CTA 1 of the small-list launch skips its first barrier
     int32_t strategy;
     int32_t use_cond;
-    int32_t pad;
+    int32_t small_edges;   // WD: lists of at most this many edges run in the persistent small-list kernel (0: off)
     cudaGraphConditionalHandle cond;
 };
 
@@ -152,6 +158,8 @@ cudaError_t launch_prepare(const StepParams &p, int32_t src, uint32_t *status, i
                            uint64_t max_steps, uint64_t time_limit_ns, cudaStream_t st);
 cudaError_t launch_init(const StepParams &p, int grid, cudaStream_t st);
 cudaError_t launch_hp_mdt(const StepParams &p, int grid, cudaStream_t st);
+cudaError_t launch_small_levels(bool sssp, const StepParams &p, int grid, cudaStream_t st);
+int small_ctas_per_sm();
 cudaError_t launch_finish_query(const StepParams &p, cudaStream_t st);
 cudaError_t launch_coo_build(const GraphDev &g, int32_t *coo_src, cudaStream_t st);
 cudaError_t launch_mdt(const GraphDev &g, int32_t bins, unsigned long long *scratch, int64_t *result,

@@ -48,7 +48,7 @@ constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
 #define LB_SERVE_MIN_BLOCKS 4
 #endif
 constexpr int kItems = LB_SERVE_ITEMS;
-constexpr int kMaxSlots = 4096;
+constexpr int kMaxSlots = 4096;  // slot indices fit 12 bits (Shared::oldest)
 constexpr uint64_t kAdmitPeriodNs = 50000;  // a busy CTA retries admission this often
 
 // Slot scheduling: 1 = round robin (after a tile a CTA moves on to the next
@@ -159,8 +159,16 @@ struct Shared {  // device-global control of the persistent kernel
     unsigned long long completed;
     unsigned long long kernel_t0;
     unsigned long long prof[8];  // per-phase cycle counters (LB_SERVE_PROFILE)
+    // oldest query in flight, as ticket << 12 | slot (kNoOldest: unknown):
+    // lowered at admission and by every scan that sees an older busy slot,
+    // reset when that query completes
+    unsigned long long oldest;
     uint32_t busy_mask[kMaxSlots / 32];  // bit s: slot s holds a query (a scan hint)
 };
+constexpr unsigned long long kNoOldest = ~0ull;
+__host__ __device__ constexpr unsigned long long oldest_pack(unsigned long long ticket, uint32_t slot) {
+    return ticket << 12 | (unsigned long long)slot;
+}
 
 struct Params {
     Slot *slots;
@@ -170,7 +178,7 @@ struct Params {
     HostShared *host;  // device view of the mapped ring
     Shared *sh;
     int32_t tile;
-    int32_t pad;
+    int32_t policy;     // 0: the oldest query's tiles first, then round robin; 1: round robin
     int64_t slot_cap;   // worklist entries per slot list
     int64_t tile_cap;   // tile starts per slot list
     int64_t slot_n;     // largest n a slot serves
@@ -295,6 +303,7 @@ __device__ void complete_query(const Params &P, Slot *S, int32_t status_code) {
     // the slot's bit leaves the busy mask before the slot is released, so a
     // later admission of the slot (which needs busy == 0) sets it again
     const uint32_t si = (uint32_t)(S - P.slots);
+    atomicCAS(&P.sh->oldest, oldest_pack(V->ticket, si), kNoOldest);
     atomicAnd(&P.sh->busy_mask[si >> 5], ~(1u << (si & 31u)));
     __threadfence();
     S->busy = 0;
@@ -483,6 +492,7 @@ __device__ void admit(const Params &P) {
         S->busy = 1;
         atomicAdd(&sh->active, 1u);
         atomicOr(&sh->busy_mask[(uint32_t)cursor >> 5], 1u << ((uint32_t)cursor & 31u));
+        if (valid) atomicMin(&sh->oldest, oldest_pack(r.ticket, (uint32_t)cursor));
         ++con;
         if (!valid) {
             complete_query(P, S, LB_ERR_ARG);
@@ -560,10 +570,46 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
             if (lane == 0) late = global_ns() - t_launch > P.hard_ns;
             late = __shfl_sync(kFull, late, 0);
             const uint32_t scan_from = s_scan_from;
-            const uint32_t nw = late ? 0u : ((uint32_t)P.nslots + 31u) >> 5;
+            uint32_t nw = late ? 0u : ((uint32_t)P.nslots + 31u) >> 5;
             const uint32_t sw = scan_from >> 5;
             int found = -1;
             uint32_t f_kind = 0, f_tiles = 0, f_tile = 0, f_q = 0;
+            unsigned long long seen_oldest = kNoOldest;  // oldest busy slot this scan saw
+            if (P.policy == 0 && !late) {
+                // the oldest query in flight first: its iterations then run as
+                // if it were alone, and the other queries fill the CTAs its
+                // current iteration leaves idle
+                int ok = 0;
+                uint32_t k2 = 0, t2 = 0, q2 = 0, idx = 0, hs = 0;
+                if (lane == 0) {
+                    const unsigned long long op = __ldcg(&P.sh->oldest);
+                    hs = (uint32_t)(op & 4095ull);
+                    if (op != kNoOldest && hs < (uint32_t)P.nslots) {
+                        Slot *S = &P.slots[hs];
+                        const unsigned long long cw = __ldcg(&S->claim);
+                        const unsigned long long jw = __ldcg(&S->job);
+                        if (job_kind(jw) != kJobNone && job_gen(jw) == (uint32_t)(cw >> 32) &&
+                            (uint32_t)cw < job_tiles(jw)) {
+                            const unsigned long long old = atomicAdd(&S->claim, 1ull);
+                            __threadfence();
+                            const unsigned long long jw2 = atomicAdd(&S->job, 0ull);
+                            k2 = job_kind(jw2);
+                            t2 = job_tiles(jw2);
+                            q2 = job_q(jw2);
+                            idx = (uint32_t)old;
+                            ok = job_gen(jw2) == (uint32_t)(old >> 32) && k2 != kJobNone && idx < t2;
+                        }
+                    }
+                }
+                if (__shfl_sync(kFull, ok, 0)) {
+                    found = (int)__shfl_sync(kFull, hs, 0);
+                    f_kind = __shfl_sync(kFull, k2, 0);
+                    f_tiles = __shfl_sync(kFull, t2, 0);
+                    f_q = __shfl_sync(kFull, q2, 0);
+                    f_tile = __shfl_sync(kFull, idx, 0);
+                    nw = 0u;
+                }
+            }
             for (uint32_t base = 0; base < nw && found < 0; base += 32) {
                 uint32_t wmask = 0;
                 if (base + lane < nw) wmask = __ldcg(&P.sh->busy_mask[(sw + base + lane) % nw]);
@@ -577,12 +623,22 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
                     const uint32_t sl = (lane + rot) & 31u;
                     const int32_t si = (int32_t)(32u * w + sl);
                     bool claimable = false;
+                    unsigned long long mine = kNoOldest;
                     if (((bits >> sl) & 1u) && si < P.nslots) {
                         const Slot *S = &P.slots[si];
                         const unsigned long long cw = __ldcg(&S->claim);
                         const unsigned long long jw = __ldcg(&S->job);
                         claimable = job_kind(jw) != kJobNone && job_gen(jw) == (uint32_t)(cw >> 32) &&
                                     (uint32_t)cw < job_tiles(jw);
+                        if (job_kind(jw) != kJobNone) mine = oldest_pack(__ldcg(&S->ticket), (uint32_t)si);
+                    }
+                    if (P.policy == 0) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const unsigned long long x = __shfl_xor_sync(kFull, mine, o);
+                            mine = x < mine ? x : mine;
+                        }
+                        seen_oldest = mine < seen_oldest ? mine : seen_oldest;
                     }
                     unsigned cand = __ballot_sync(kFull, claimable);
                     while (cand) {
@@ -617,6 +673,9 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
                 }
             }
             if (lane == 0) {
+                // the hint catches up with the oldest busy slot any scan sees
+                if (seen_oldest != kNoOldest && seen_oldest < __ldcg(&P.sh->oldest))
+                    atomicMin(&P.sh->oldest, seen_oldest);
                 if (found >= 0) s_scan_from = (uint32_t)found;
                 s_slot = found;
                 s_exit = late;
@@ -826,6 +885,7 @@ lb_status launch_kernel(lb_server *s) {
     P.host = s->d_ring;
     P.sh = s->d_shared;
     P.tile = s->opt.tile;
+    P.policy = s->opt.policy;
     P.slot_cap = s->slot_cap;
     P.tile_cap = s->tile_cap;
     P.slot_n = s->slot_n;
@@ -878,7 +938,8 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     if (o.mem_fraction <= 0.0) o.mem_fraction = 0.5;
     if (o.launch_ms == 0) o.launch_ms = 600000;
     if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > kMaxSlots || o.idle_us < 0 ||
-        o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32 || o.launch_ms < 0) {
+        o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32 || o.launch_ms < 0 || o.policy < 0 ||
+        o.policy > 1) {
         delete s;
         return sfail(LB_ERR_ARG, "bad server options");
     }
@@ -937,6 +998,7 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     if (e == cudaSuccess) e = cudaMemcpy(s->d_graphs, gd.data(), sizeof(GraphDev) * gd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_shared, sizeof(Shared));
     if (e == cudaSuccess) e = cudaMemset(s->d_shared, 0, sizeof(Shared));
+    if (e == cudaSuccess) e = cudaMemset(&s->d_shared->oldest, 0xFF, sizeof(unsigned long long));  // kNoOldest
     std::vector<Slot> hs((size_t)s->nslots);
     for (int32_t i = 0; i < s->nslots && e == cudaSuccess; ++i) {
         Slot &S = hs[(size_t)i];

@@ -10,19 +10,15 @@
 
 #include "lb_device.cuh"
 
+// CTAs per SM the WD relax is compiled for (40 registers at 6), BFS and
+// SSSP.  Measured on R-MAT scale 24 with the windowed walk and 3 edges per
+// lane per round: BFS 2.08 / 2.19 / 2.48 ms at 6 / 5 / 4 CTAs, SSSP 9.37 /
+// 9.39 / 10.6 ms.
 #ifndef LB_WD_MIN_BLOCKS
 #define LB_WD_MIN_BLOCKS 6
 #endif
-// SSSP relax: 5 CTAs per SM (48 registers) with 3 edges per thread per
-// round, 3.6% faster at R-MAT scale 24 than 6 CTAs (40 registers) with 2.
 #ifndef LB_WD_MIN_BLOCKS_SSSP
-#define LB_WD_MIN_BLOCKS_SSSP 5
-#endif
-// Whether the SSSP walk keeps its look-ahead window across steps and skips
-// the boundary search inside one adjacency list, as the BFS walk does (it
-// needs more registers in the SSSP kernel, which also loads the source id).
-#ifndef LB_WD_FAST_SSSP
-#define LB_WD_FAST_SSSP 1
+#define LB_WD_MIN_BLOCKS_SSSP 6
 #endif
 // Column and weight streams loaded evict-first (ld.global.cs) so the
 // randomly read distance, queued and visited lines keep their place in L2
@@ -37,48 +33,11 @@ __device__ __forceinline__ T ld_edge(const T *p) {
     return kStream ? __ldcs(p) : __ldg(p);
 }
 
-// BFS walks with 32-bit indices (wd_walk_tile32): 8% faster at R-MAT
-// scale 24 than the 64-bit walk.  A run starts only where the current list
-// reaches more than LB_WD_RUN_MIN_BFS edges ahead (>= 32): shorter lists go
-// through boundary steps, whose groups are always full.
-#ifndef LB_WD_RUN_MIN_BFS
-#define LB_WD_RUN_MIN_BFS 32
-#endif
-#ifndef LB_WD_IDX32
-#define LB_WD_IDX32 1
-#endif
-// BFS walks with wd_walk_bfs (a 64-entry window of the list in registers,
-// the lean relax) instead of wd_walk_tile32.
-#ifndef LB_BFS_WALK2
-#define LB_BFS_WALK2 0
-#endif
-// BFS walk relaxes with relax_bfs_lean (warp-uniform early exits, one push
-// per group, flushes only when a group's pushes would not fit) instead of
-// the staged relax shared with SSSP.
-#ifndef LB_BFS_LEAN
-#define LB_BFS_LEAN 0
-#endif
-
 // The final flush of a WD iteration (and of a serving RELAX tile) as one
 // list reservation per CTA (wflush_block) instead of one per warp.
 #ifndef LB_BLOCK_FLUSH
 #define LB_BLOCK_FLUSH 1
 #endif
-
-// Warp-wide 32-way search for a warp's first list entry (bit mask: 1 = the
-// BFS walk, 2 = the SSSP walk) instead of a per-warp binary search.
-#ifndef LB_WD_WARP_SEARCH
-#define LB_WD_WARP_SEARCH 3
-#endif
-
-// L2 prefetch in the walk (bit mask): 1 = a BFS run's edge range with one
-// bulk prefetch, 2 = the first line of every look-ahead entry's adjacency
-// list.  Measured on R-MAT scale 24: 1 gains 2% on BFS (neutral for SSSP,
-// so SSSP does not use it), 2 costs 25-60% on levels with short lists.
-#ifndef LB_WD_PREFETCH
-#define LB_WD_PREFETCH 1
-#endif
-
 
 namespace lbk {
 
@@ -300,208 +259,24 @@ __device__ __forceinline__ KT warp_search(const int32_t *scan, KT lo, KT hi, IT 
     return lo;
 }
 
-// The walk of one tile with 32-bit list edges, list positions and edge
-// ids (all < 2^31, checked when the graph is created; edge-id arithmetic
-// wraps mod 2^32).  Used for BFS.
-template <bool SSSP, int STEPS, bool COH>
-__device__ __forceinline__ void wd_walk_tile32(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
-                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
-                                             uint32_t *status, uint32_t level, uint32_t *err,
-                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
-    const int64_t q = T / kTileGrain;
-    const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
-    const int64_t ntiles = (E + T - 1) / T;
-    const uint32_t lane = lane_id();
-    const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
-    const int64_t e0 = t * T;
-    const int64_t e1 = min(e0 + T, E);
-    int64_t i0 = ld_list<COH>(in.tstart + t * q);
-    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)ld_list<COH>(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
-    if (i0 < 0 || i0 >= ihi) {
-        if (lane == 0) atomicOr(err, kErrBounds);
-        return;
-    }
-    using IT = uint32_t;  // list edges and edge ids
-    using KT = int32_t;   // list positions
-    const int64_t w064 = e0 + (int64_t)warp * W;
-    if (w064 >= e1) return;  // warp-uniform
-    const IT w0 = (IT)w064;
-    const IT w1 = (IT)min(w064 + W, e1);
-    const KT ihiK = (KT)ihi;
-    KT kcur = (LB_WD_WARP_SEARCH & 1) ? warp_search<COH, IT, KT>(in.scan, (KT)i0, ihiK, w0, lane) : (KT)i0;
-    if (!(LB_WD_WARP_SEARCH & 1)) {
-        KT lo = (KT)i0, hi = ihiK;  // entry of the slice's first edge
-        while (hi - lo > 1) {
-            const KT mid = (KT)(((uint64_t)lo + (uint64_t)hi) >> 1);
-            if ((IT)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
-        }
-        kcur = lo;
-    }
-    int32_t scur = ld_list<COH>(in.scan + kcur);
-    int32_t bcur = ld_list<COH>(in.beg + kcur);
-    int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
-    // look-ahead window: lane l holds entry kcur + 1 + l; it stays valid
-    // until the walk advances, so steps inside one long adjacency list
-    // (most edges of a skewed graph) load no list entries at all
-    constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
-    constexpr int R = STEPS;
-    static_assert(32 * R <= kWB - ((!SSSP && LB_BFS_LEAN) ? 0 : 32), "push buffer too small for one group");
-    int32_t sj = INT32_MAX, bj = 0, uj = 0;
-    bool fresh = false;
-    // the walk produces one group of R x 32 edges per pass, either from a
-    // run (consecutive edges of entry kcur, loaded with a plain strided
-    // loop) or from the general step (entry boundaries inside the group),
-    // and relaxes every group at one call site
-    IT ew = w0;      // next list edge
-    IT rend = 0;     // end of the current run (exclusive)
-    IT rbase = 0;    // edge id = rbase + list edge inside the run
-    bool in_run = false;
-    bool radv = false;     // the run ends where entry kcur + 1 starts
-    uint32_t rdu = 0;      // SSSP: distance the run's source relaxes with
-    while (ew < w1) {  // warp-uniform
-        int32_t vv[R];
-        uint32_t ww[R], dd[R];
-        bool ok[R];
-        if (!fresh) {
-            const KT j = kcur + 1 + (KT)lane;
-            sj = INT32_MAX;
-            bj = 0;
-            uj = 0;
-            if (j < ihiK) {
-                sj = ld_list<COH>(in.scan + j);
-                bj = ld_list<COH>(in.beg + j);
-                if (SSSP) uj = ld_list<COH>(in.v + j);
-                if ((LB_WD_PREFETCH & 2) && (uint64_t)bj < (uint64_t)g.m) {
-                    prefetch_l2(g.col + bj);
-                    if (SSSP) prefetch_l2(g.w + bj);
-                }
-            }
-            fresh = true;
-        }
-        if (kFast && !in_run) {
-            // first edge of entry kcur + 1: when no entry starts inside the
-            // next 32 edges, run through entry kcur's edges up to that start
-            const IT s_next = (IT)__shfl_sync(kFull, sj, 0);
-            if (s_next > ew + (IT)LB_WD_RUN_MIN_BFS) {
-                rend = s_next < w1 ? s_next : w1;
-                radv = s_next <= w1;
-                if ((int64_t)bcur + ((int64_t)ew - scur) < 0 || (int64_t)bcur + ((int64_t)rend - scur) > g.m) {
-                    if (lane == 0) atomicOr(err, kErrBounds);
-                    return;
-                }
-                rbase = (IT)bcur - (IT)scur;
-                in_run = true;
-                if ((LB_WD_PREFETCH & 1) && !SSSP && lane == 0 && rend - ew > (IT)(32 * R))
-                    bulk_prefetch_l2(g.col + (rbase + ew + (IT)(32 * R)), g.col + (rbase + rend), g.col + g.m);
-                if (SSSP) rdu = is_queued<COH>(qcur, ucur) ? kInf : ld_mut<COH>(status + ucur);
-            }
-        }
-        if (in_run) {
-#pragma unroll
-            for (int st = 0; st < R; ++st) {
-                const IT e = ew + (IT)(32 * st) + (IT)lane;
-                ok[st] = e < rend;
-                vv[st] = ok[st] ? ld_edge<SSSP>(g.col + (rbase + e)) : 0;
-                ww[st] = (SSSP && ok[st]) ? ld_edge<SSSP>(g.w + (rbase + e)) : 0u;
-                dd[st] = rdu;
-            }
-            ew = ew + (IT)(32 * R) < rend ? ew + (IT)(32 * R) : rend;
-            if (ew == rend) {
-                if (radv) {  // entry kcur + 1 starts at ew
-                    scur = (int32_t)rend;
-                    bcur = __shfl_sync(kFull, bj, 0);
-                    if (SSSP) ucur = __shfl_sync(kFull, uj, 0);
-                    kcur += 1;
-                    fresh = false;
-                }
-                in_run = false;
-            }
-        } else {
-#pragma unroll
-            for (int st = 0; st < R; ++st) {
-                const IT es = ew + (IT)(32 * st);  // first edge of this step (uniform)
-                const IT e = es + (IT)lane;
-                ok[st] = false;
-                vv[st] = 0;
-                ww[st] = 0;
-                dd[st] = 0;
-                if (es >= w1) continue;  // warp-uniform
-                if (!fresh) {  // the previous step advanced
-                    const KT j = kcur + 1 + (KT)lane;
-                    sj = INT32_MAX;
-                    bj = 0;
-                    uj = 0;
-                    if (j < ihiK) {
-                        sj = ld_list<COH>(in.scan + j);
-                        bj = ld_list<COH>(in.beg + j);
-                        if (SSSP) uj = ld_list<COH>(in.v + j);
-                    }
-                    fresh = true;
-                }
-                int32_t s_l = scur, b_l = bcur, u_l = ucur;
-                const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es
-                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
-                const int c = __popc(starts & upto);
-                const int src_lane = c > 0 ? c - 1 : 0;
-                const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
-                const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
-                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
-                if (c > 0) {
-                    s_l = s_sh;
-                    b_l = b_sh;
-                    u_l = u_sh;  // taken before the walk advances
-                }
-                // advance to the entry holding the next step's first edge
-                const int adv = __popc(__ballot_sync(kFull, (IT)sj <= es + 32));
-                if (adv > 0) {
-                    scur = __shfl_sync(kFull, sj, adv - 1);
-                    bcur = __shfl_sync(kFull, bj, adv - 1);
-                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
-                    kcur += adv;
-                    fresh = false;
-                }
-                if (e < w1) {
-                    const IT eidx = (IT)b_l + (e - (IT)s_l);
-                    if ((uint64_t)eidx >= (uint64_t)g.m) {  // a wrapped 32-bit index is >= 2^31 > m
-                        atomicOr(err, kErrBounds);
-                    } else {
-                        ok[st] = true;
-                        vv[st] = ld_edge<SSSP>(g.col + eidx);
-                        if (SSSP) {
-                            ww[st] = ld_edge<SSSP>(g.w + eidx);
-                            dd[st] = is_queued<COH>(qcur, u_l) ? kInf : ld_mut<COH>(status + u_l);
-                        }
-                    }
-                }
-            }
-            ew += (IT)(32 * R);
-        }
-        if constexpr (!SSSP && LB_BFS_LEAN) {
-            relax_bfs_lean<R, COH>(ok, vv, g.off, bitmap, status, level, wb, ws, cnt, o);
-        } else {
-            if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
-            relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, qcur, status, level, err,
-                                                             wb, ws, cnt, o);
-        }
-    }
-}
-
-// BFS walk of one tile with a 64-entry window of the list in registers.
-// Lane l holds entries kb + l and kb + 32 + l (first list edge s and the
-// delta d = first CSR edge - s, so an edge's CSR index is d + list edge);
-// the current entry kcur stays within the window's first half, and the
-// window slides by 32 entries when kcur leaves it (one reload per 32
-// entries, not per step).  A group of R x 32 edges that lies inside entry
-// kcur is loaded directly; otherwise each 32-edge step finds every lane's
-// entry from the bit mask of entry starts inside the step (an entry has at
-// least one edge, so at most 32 start in 32 positions).  The relax is
-// relax_bfs_lean.  32-bit list edges and edge ids (< 2^31).
-template <int R, bool COH>
-__device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
-                                            int64_t T, int64_t t, uint32_t *bitmap, uint32_t *status,
-                                            uint32_t level, uint32_t *err, WarpBuf &wb, WarpScratch &ws,
-                                            uint32_t &cnt, const FlushOut &o) {
+// The walk of one tile with a 64-entry window of the list in registers.
+// Lane l holds entries kb + l and kb + 32 + l: the entry's first list edge
+// s, the delta d = first CSR edge - s (an edge's CSR index is d + list
+// edge) and, for SSSP, the distance du its edges relax with (kInf when the
+// entry's node has been queued again in this iteration: the next one
+// expands it with the newer value).  The current entry kcur stays within
+// the window's first half, and the window slides by 32 entries when kcur
+// leaves it: one reload per 32 entries, not per step.  A group of R x 32
+// edges that lies inside entry kcur is loaded directly; otherwise each
+// 32-edge step finds every lane's entry from the bit mask of entry starts
+// inside the step (an entry has at least one edge, so at most 32 start in
+// 32 positions) and takes its fields from the window by shuffle.  32-bit
+// list edges and edge ids (< 2^31, checked when the graph is created).
+template <bool SSSP, int R, bool COH>
+__device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
+                                            int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
+                                            uint32_t *status, uint32_t level, uint32_t *err, WarpBuf &wb,
+                                            WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
     const int64_t q = T / kTileGrain;
     const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
     const int64_t ntiles = (E + T - 1) / T;
@@ -526,23 +301,33 @@ __device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &i
     int32_t kcur = warp_search<COH, uint32_t, int32_t>(in.scan, (int32_t)i0, ihiK, (uint32_t)w0, lane);
     int32_t kb = kcur;
     int32_t s0 = INT32_MAX, d0 = 0, s1 = INT32_MAX, d1 = 0;
-    {
-        const int32_t j0 = kb + (int32_t)lane, j1 = j0 + 32;
-        if (j0 < ihiK) { s0 = ld_list<COH>(in.scan + j0); d0 = ld_list<COH>(in.beg + j0) - s0; }
-        if (j1 < ihiK) { s1 = ld_list<COH>(in.scan + j1); d1 = ld_list<COH>(in.beg + j1) - s1; }
-    }
+    uint32_t u0 = kInf, u1 = kInf;  // SSSP: distance the entry relaxes with
+    auto load = [&](int32_t j, int32_t &sj, int32_t &dj, uint32_t &uj) {
+        sj = INT32_MAX;
+        dj = 0;
+        uj = kInf;
+        if (j < ihiK) {
+            sj = ld_list<COH>(in.scan + j);
+            dj = ld_list<COH>(in.beg + j) - sj;
+            if (SSSP) {
+                const int32_t u = ld_list<COH>(in.v + j);
+                if (u >= 0 && (int64_t)u < g.n) uj = is_queued<COH>(qcur, u) ? kInf : ld_mut<COH>(status + u);
+            }
+        }
+    };
+    load(kb + (int32_t)lane, s0, d0, u0);
+    load(kb + 32 + (int32_t)lane, s1, d1, u1);
     int32_t ew = w0;
     while (ew < w1) {  // warp-uniform
         bool ok[R];
         int32_t vv[R];
+        uint32_t ww[R], dd[R];
         if (kcur >= kb + 32) {  // slide: the second half becomes the first
             kb += 32;
             s0 = s1;
             d0 = d1;
-            const int32_t j1 = kb + 32 + (int32_t)lane;
-            s1 = INT32_MAX;
-            d1 = 0;
-            if (j1 < ihiK) { s1 = ld_list<COH>(in.scan + j1); d1 = ld_list<COH>(in.beg + j1) - s1; }
+            u0 = u1;
+            load(kb + 32 + (int32_t)lane, s1, d1, u1);
         }
         // start of entry kcur + 1 (window position 1..32)
         const int32_t pn = kcur + 1 - kb;
@@ -551,6 +336,7 @@ __device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &i
             // the whole group lies inside entry kcur
             const int32_t pc = kcur - kb;
             const int32_t dcur = __shfl_sync(kFull, d0, pc);
+            const uint32_t ducur = SSSP ? __shfl_sync(kFull, u0, pc) : 0u;
             if (dcur + ew < 0 || dcur + min(ew + 32 * R, w1) > m) {
                 if (lane == 0) atomicOr(err, kErrBounds);
                 return;
@@ -559,7 +345,9 @@ __device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &i
             for (int r = 0; r < R; ++r) {
                 const int32_t e = ew + 32 * r + (int32_t)lane;
                 ok[r] = e < w1;
-                vv[r] = ok[r] ? ld_edge<false>(g.col + (dcur + e)) : 0;
+                vv[r] = ok[r] ? ld_edge<SSSP>(g.col + (dcur + e)) : 0;
+                ww[r] = (SSSP && ok[r]) ? ld_edge<SSSP>(g.w + (dcur + e)) : 0u;
+                dd[r] = ducur;
             }
             ew += 32 * R;
             if (s_next == ew) kcur += 1;
@@ -568,22 +356,29 @@ __device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &i
             for (int r = 0; r < R; ++r) {
                 ok[r] = false;
                 vv[r] = 0;
+                ww[r] = 0u;
+                dd[r] = 0u;
                 if (ew >= w1) continue;  // warp-uniform
                 if (kcur >= kb + 32) {
                     kb += 32;
                     s0 = s1;
                     d0 = d1;
-                    const int32_t j1 = kb + 32 + (int32_t)lane;
-                    s1 = INT32_MAX;
-                    d1 = 0;
-                    if (j1 < ihiK) { s1 = ld_list<COH>(in.scan + j1); d1 = ld_list<COH>(in.beg + j1) - s1; }
+                    u0 = u1;
+                    load(kb + 32 + (int32_t)lane, s1, d1, u1);
                 }
                 const int32_t p0 = s0 - ew, p1 = s1 - ew;  // entries starting after ew have p > 0
-                const uint32_t bits = ((p0 > 0 && p0 < 32) ? (1u << p0) : 0u) | ((p1 > 0 && p1 < 32) ? (1u << p1) : 0u);
+                const uint32_t bits =
+                    ((p0 > 0 && p0 < 32) ? (1u << p0) : 0u) | ((p1 > 0 && p1 < 32) ? (1u << p1) : 0u);
                 const uint32_t starts = __reduce_or_sync(kFull, bits);
                 const int32_t pe = kcur - kb + __popc(starts & upto);  // window position of my entry
                 const int32_t x0 = __shfl_sync(kFull, d0, pe & 31);
                 const int32_t x1 = __shfl_sync(kFull, d1, pe & 31);
+                uint32_t du = 0u;
+                if (SSSP) {
+                    const uint32_t y0 = __shfl_sync(kFull, u0, pe & 31);
+                    const uint32_t y1 = __shfl_sync(kFull, u1, pe & 31);
+                    du = pe < 32 ? y0 : y1;
+                }
                 const int32_t e = ew + (int32_t)lane;
                 const int32_t eidx = (pe < 32 ? x0 : x1) + e;
                 if (e < w1) {
@@ -591,7 +386,11 @@ __device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &i
                         atomicOr(err, kErrBounds);
                     } else {
                         ok[r] = true;
-                        vv[r] = ld_edge<false>(g.col + eidx);
+                        vv[r] = ld_edge<SSSP>(g.col + eidx);
+                        if (SSSP) {
+                            ww[r] = ld_edge<SSSP>(g.w + eidx);
+                            dd[r] = du;
+                        }
                     }
                 }
                 // the entry holding the next step's first edge
@@ -599,205 +398,25 @@ __device__ __forceinline__ void wd_walk_bfs(const GraphDev &g, const NodeList &i
                 ew += 32;
             }
         }
-        relax_bfs_lean<R, COH>(ok, vv, g.off, bitmap, status, level, wb, ws, cnt, o);
-    }
-}
-
-// The walk of one tile with 64-bit list edges and edge ids.  Used for SSSP:
-// its kernel runs slower with the 32-bit form of the same loop (22% at
-// R-MAT scale 24), and slower still with that loop at 64-bit width.
-template <bool SSSP, int STEPS, bool COH>
-__device__ __forceinline__ void wd_walk_tile64(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
-                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
-                                             uint32_t *status, uint32_t level, uint32_t *err,
-                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
-    const int64_t q = T / kTileGrain;
-    const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
-    const int64_t ntiles = (E + T - 1) / T;
-    const uint32_t lane = lane_id();
-    const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
-    const int64_t e0 = t * T;
-    const int64_t e1 = min(e0 + T, E);
-    int64_t i0 = ld_list<COH>(in.tstart + t * q);
-    int64_t ihi = (t + 1 < ntiles) ? min((int64_t)ld_list<COH>(in.tstart + (t + 1) * q) + 1, in_cnt) : in_cnt;
-    if (i0 < 0 || i0 >= ihi) {
-        if (lane == 0) atomicOr(err, kErrBounds);
-        return;
-    }
-    const int64_t w0 = e0 + (int64_t)warp * W;
-    const int64_t w1 = min(w0 + W, e1);
-    if (w0 >= w1) return;  // warp-uniform
-    int64_t kcur = i0;
-    if (LB_WD_WARP_SEARCH & 2) {
-        kcur = warp_search<COH, int64_t, int64_t>(in.scan, i0, ihi, w0, lane);
-    } else {
-        int64_t lo = i0, hi = ihi;  // entry of the slice's first edge
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)ld_list<COH>(in.scan + mid) <= w0) lo = mid; else hi = mid;
-        }
-        kcur = lo;
-    }
-    int32_t scur = ld_list<COH>(in.scan + kcur);
-    int32_t bcur = ld_list<COH>(in.beg + kcur);
-    int32_t ucur = SSSP ? ld_list<COH>(in.v + kcur) : 0;
-    // look-ahead window: lane l holds entry kcur + 1 + l; it stays valid
-    // until the walk advances, so steps inside one long adjacency list
-    // (most edges of a skewed graph) load no list entries at all
-    constexpr bool kFast = !SSSP || LB_WD_FAST_SSSP;
-    constexpr int R = STEPS;
-    static_assert(32 * R <= kWB - 32, "push buffer too small for one group");
-    int32_t sj = INT32_MAX, bj = 0, uj = 0;
-    bool fresh = false;
-    // the walk produces one group of R x 32 edges per pass, either from a
-    // run (consecutive edges of entry kcur, loaded with a plain strided
-    // loop) or from the general step (entry boundaries inside the group),
-    // and relaxes every group at one call site
-    int64_t ew = w0;    // next list edge
-    int64_t rend = -1;  // end of the current run (exclusive); -1: no run
-    int64_t rbase = 0;  // edge id = rbase + list edge inside the run
-    bool radv = false;  // the run ends where entry kcur + 1 starts
-    uint32_t rdu = 0;   // SSSP: distance the run's source relaxes with
-    while (ew < w1) {  // warp-uniform
-        int32_t vv[R];
-        uint32_t ww[R], dd[R];
-        bool ok[R];
-        if (!fresh) {
-            const int64_t j = kcur + 1 + lane;
-            sj = INT32_MAX;
-            bj = 0;
-            uj = 0;
-            if (j < ihi) {
-                sj = ld_list<COH>(in.scan + j);
-                bj = ld_list<COH>(in.beg + j);
-                if (SSSP) uj = ld_list<COH>(in.v + j);
-                if ((LB_WD_PREFETCH & 2) && (uint32_t)bj < (uint64_t)g.m) {
-                    prefetch_l2(g.col + bj);
-                    if (SSSP) prefetch_l2(g.w + bj);
-                }
-            }
-            fresh = true;
-        }
-        if (kFast && rend < 0) {
-            // first edge of entry kcur + 1: when no entry starts inside the
-            // next 32 edges, run through entry kcur's edges up to that start
-            const int64_t s_next = (int64_t)__shfl_sync(kFull, sj, 0);
-            if (s_next > ew + 32) {
-                rend = min(s_next, w1);
-                radv = s_next <= w1;
-                rbase = (int64_t)bcur - (int64_t)scur;
-                if (rbase + ew < 0 || rbase + rend > g.m) {
-                    if (lane == 0) atomicOr(err, kErrBounds);
-                    return;
-                }
-                if ((LB_WD_PREFETCH & 1) && !SSSP && lane == 0 && rend - ew > 32 * R)
-                    bulk_prefetch_l2(g.col + (rbase + ew + 32 * R), g.col + (rbase + rend), g.col + g.m);
-                if (SSSP) rdu = is_queued<COH>(qcur, ucur) ? kInf : ld_mut<COH>(status + ucur);
-            }
-        }
-        if (rend >= 0) {
-#pragma unroll
-            for (int st = 0; st < R; ++st) {
-                const int64_t e = ew + 32 * st + lane;
-                ok[st] = e < rend;
-                vv[st] = ok[st] ? ld_edge<SSSP>(g.col + (rbase + e)) : 0;
-                ww[st] = (SSSP && ok[st]) ? ld_edge<SSSP>(g.w + (rbase + e)) : 0u;
-                dd[st] = rdu;
-            }
-            ew = min(ew + 32 * R, rend);
-            if (ew == rend) {
-                if (radv) {  // entry kcur + 1 starts at ew
-                    scur = (int32_t)rend;
-                    bcur = __shfl_sync(kFull, bj, 0);
-                    if (SSSP) ucur = __shfl_sync(kFull, uj, 0);
-                    kcur += 1;
-                    fresh = false;
-                }
-                rend = -1;
-            }
+        if constexpr (SSSP) {
+            if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
+            relax_items<true, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, qcur, status, level, err,
+                                                             wb, ws, cnt, o);
         } else {
-#pragma unroll
-            for (int st = 0; st < R; ++st) {
-                const int64_t es = ew + 32 * st;  // first edge of this step (uniform)
-                const int64_t e = es + lane;
-                ok[st] = false;
-                vv[st] = 0;
-                ww[st] = 0;
-                dd[st] = 0;
-                if (es >= w1) continue;  // warp-uniform
-                if (!fresh) {  // the previous step advanced
-                    const int64_t j = kcur + 1 + lane;
-                    sj = INT32_MAX;
-                    bj = 0;
-                    uj = 0;
-                    if (j < ihi) {
-                        sj = ld_list<COH>(in.scan + j);
-                        bj = ld_list<COH>(in.beg + j);
-                        if (SSSP) uj = ld_list<COH>(in.v + j);
-                    }
-                    fresh = true;
-                }
-                int32_t s_l = scur, b_l = bcur, u_l = ucur;
-                const int32_t pos = sj - (int32_t)es;  // >= 1: entry j starts after es (es < 2^31)
-                const uint32_t starts = __reduce_or_sync(kFull, pos < 32 ? (1u << pos) : 0u);
-                const int c = __popc(starts & upto);
-                const int src_lane = c > 0 ? c - 1 : 0;
-                const int32_t s_sh = __shfl_sync(kFull, sj, src_lane);
-                const int32_t b_sh = __shfl_sync(kFull, bj, src_lane);
-                const int32_t u_sh = SSSP ? __shfl_sync(kFull, uj, src_lane) : 0;
-                if (c > 0) {
-                    s_l = s_sh;
-                    b_l = b_sh;
-                    u_l = u_sh;  // taken before the walk advances
-                }
-                // advance to the entry holding the next step's first edge
-                const int adv = __popc(__ballot_sync(kFull, (int64_t)sj <= es + 32));
-                if (adv > 0) {
-                    scur = __shfl_sync(kFull, sj, adv - 1);
-                    bcur = __shfl_sync(kFull, bj, adv - 1);
-                    if (SSSP) ucur = __shfl_sync(kFull, uj, adv - 1);
-                    kcur += adv;
-                    fresh = false;
-                }
-                if (e < w1) {
-                    const int64_t eidx = (int64_t)b_l + (e - (int64_t)s_l);
-                    if ((uint64_t)eidx >= (uint64_t)g.m) {
-                        atomicOr(err, kErrBounds);
-                    } else {
-                        ok[st] = true;
-                        vv[st] = ld_edge<SSSP>(g.col + eidx);
-                        if (SSSP) {
-                            ww[st] = ld_edge<SSSP>(g.w + eidx);
-                            dd[st] = is_queued<COH>(qcur, u_l) ? kInf : ld_mut<COH>(status + u_l);
-                        }
-                    }
-                }
-            }
-            ew += 32 * R;
+            relax_bfs_lean<R, COH>(ok, vv, g.off, bitmap, status, level, wb, ws, cnt, o);
         }
-        if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
-        relax_items<SSSP, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, qcur, status, level, err, wb,
-                                                         ws, cnt, o);
     }
 }
 
 // One tile of the walk.  COH selects L2-coherent loads for everything other
-// CTAs write (the persistent serving kernel); the single-query launches use
-// the read-only / L1 paths.
+// CTAs write (the persistent serving and small-list kernels); the
+// single-level launches use the read-only / L1 paths.
 template <bool SSSP, int STEPS, bool COH>
 __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
                                              int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
-                                             uint32_t *status, uint32_t level, uint32_t *err,
-                                             WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
-    if constexpr (!SSSP && LB_BFS_WALK2)
-        wd_walk_bfs<STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, status, level, err, wb, ws, cnt, o);
-    else if constexpr (!SSSP && LB_WD_IDX32)
-        wd_walk_tile32<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, qcur, status, level, err, wb, ws,
-                                         cnt, o);
-    else
-        wd_walk_tile64<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, qcur, status, level, err, wb, ws,
-                                         cnt, o);
+                                             uint32_t *status, uint32_t level, uint32_t *err, WarpBuf &wb,
+                                             WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+    wd_walk_win<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, qcur, status, level, err, wb, ws, cnt, o);
 }
 
 template <bool SSSP, int STEPS>
@@ -816,6 +435,9 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
     Ctl *ctl = p.ctl;
+    // the small-list kernel that runs before this step in the device loop
+    // may have finished the query (uniform: every CTA reads the same flag)
+    if (p.small_edges > 0 && ctl->active == 0u) return;
     const uint32_t par = ctl->par;
     const int64_t in_cnt = ctl->in_cnt;
     const int64_t E = (int64_t)ctl->in_edges;
@@ -843,6 +465,175 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
 #endif
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
+}
+
+// ---------------------------------------------------------------------------
+// Small-list levels in one persistent launch (WD).  A high-diameter graph
+// (a grid: thousands of levels of a few thousand edges) spends most of a
+// level on the launch and the end-of-step protocol, not on edges.  While
+// the input list has at most p.small_edges edges, this kernel (one CTA per
+// SM, launched cooperatively so that every CTA is resident) runs level
+// after level: the workload-decomposition walk over the list, a block-wide
+// flush into the output list, then a grid barrier, after which every CTA
+// reads the output list's size and continues with it.  It leaves the loop
+// state in the control block when the list empties, grows past the limit,
+// or a cap is reached; the regular WD step runs the large levels.  Level L
+// counts its pushes in small_pack[L % 3]; CTA 0 zeroes the counter of level
+// L + 1 during level L (its last reads were right after the barrier ending
+// level L - 2, and every CTA has passed the barrier ending level L - 1
+// since), and all three after a last barrier before the launch returns, so
+// they start at zero in every launch.  Data other CTAs write during the
+// launch is read through L2.
+// The barrier's wait is bounded: after kBarrierLimitNs a CTA records
+// kErrDeadline, ends the device loop and returns, so a barrier that cannot
+// complete ends the query with LB_ERR_TIMEOUT instead of a hang.
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;
+
+// Grid barrier among the launch's CTAs (every thread calls it).  Returns
+// false when the wait ran past kBarrierLimitNs; *stop receives the
+// releasing CTA's verdict on the query's time limit.
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, bool *stop) {
+    __shared__ uint32_t s_ok, s_stop;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t gen = *(volatile uint32_t *)&ctl->bar_gen;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&ctl->bar_count, 1u);
+        uint32_t ok = 1u;
+        if (arrived == gridDim.x - 1) {
+            ctl->bar_count = 0u;
+            ctl->bar_stop = global_ns() > ctl->t_deadline ? 1u : 0u;
+            __threadfence();
+            atomicExch(&ctl->bar_gen, gen + 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*(volatile uint32_t *)&ctl->bar_gen == gen) {
+                if (global_ns() - t0 > kBarrierLimitNs) {
+                    ok = 0u;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+        s_stop = *(volatile uint32_t *)&ctl->bar_stop;
+    }
+    __syncthreads();
+    *stop = s_stop != 0u;
+    return s_ok != 0u;
+}
+
+#ifndef LB_SMALL_CTAS
+#define LB_SMALL_CTAS 1
+#endif
+template <bool SSSP, int ITEMS>
+__global__ void __launch_bounds__(kBlock, LB_SMALL_CTAS) k_small_levels(StepParams p) {
+    __shared__ WarpBuf s_wb[kWarps];
+    __shared__ WarpScratch s_ws[kWarps];
+    Ctl *ctl = p.ctl;
+    const int64_t lim = p.small_edges;
+    uint32_t level = *(volatile uint32_t *)&ctl->level;
+    uint32_t par = *(volatile uint32_t *)&ctl->par;
+    int64_t in_cnt = *(volatile uint32_t *)&ctl->in_cnt;
+    int64_t E = (int64_t)*(volatile uint64_t *)&ctl->in_edges;
+    // uniform: every CTA reads the same state left by the previous launch
+    if (lim <= 0 || *(volatile uint32_t *)&ctl->active == 0u || in_cnt == 0 || E > lim) return;
+    uint32_t *status = ctl->status;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint64_t step0 = ctl->step;
+    const uint32_t max_levels = ctl->max_levels;
+    uint64_t steps = 0;
+    bool failed = false;
+    for (;;) {
+        uint32_t *const qcur = queued_half(p.bitmap, p.bm_words, level);
+        const NodeList in = p.lists[par];
+        if (SSSP) {
+            // the other half holds the bits of the previous level, whose queued
+            // vertices with out-edges are exactly this level's entries (bits of
+            // vertices without out-edges are never read): clear those
+            uint32_t *qn = queued_half(p.bitmap, p.bm_words, level + 1u);
+            const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+            for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < in_cnt; k += stride) {
+                const int32_t u = __ldcg(in.v + k);
+                if (u >= 0 && (int64_t)u < p.g.n) atomicAnd(&qn[(uint32_t)u >> 5], ~(1u << ((uint32_t)u & 31u)));
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->small_pack[(level + 1u) % 3u] = 0ull;
+        FlushOut o;
+        o.list = p.lists[par ^ 1u];
+        o.elist = nullptr;
+        o.pack = &ctl->small_pack[level % 3u];
+        o.cap = p.list_cap;
+        o.tile_cap = p.tile_cap;
+        o.tile = (int32_t)kTileGrain;
+        o.mdt = p.mdt;
+        o.err = &ctl->error;
+        o.pushes = &ctl->pushes;
+        o.child_first = nullptr;
+        uint32_t cnt = 0;
+        const int64_t T = iteration_tile(E, gridDim.x, p.tile);
+        const int64_t ntiles = (E + T - 1) / T;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+            wd_walk_tile<SSSP, ITEMS, true>(p.g, in, in_cnt, E, T, t, p.bitmap, qcur, status, level, &ctl->error,
+                                            s_wb[warp], s_ws[warp], cnt, o);
+        wflush_block<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
+        // test hook: one CTA that never arrives makes the others' waits run out
+        if (p.test_barrier_skip && blockIdx.x == 1) return;
+        bool stop = false;
+        if (!grid_barrier(ctl, &stop)) {
+            failed = true;
+            break;
+        }
+        const unsigned long long pk = __ldcg(&ctl->small_pack[level % 3u]);
+        int64_t ncnt = (int64_t)(pk >> 32);
+        const int64_t nedges = (int64_t)(pk & 0xFFFFFFFFull);
+        if (ncnt > p.list_cap) {
+            if (threadIdx.x == 0) atomicOr(&ctl->error, kErrCapacity);
+            ncnt = p.list_cap;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint32_t tl = ctl->trace_len;
+            if (tl < (uint32_t)kTraceMax) {
+                ctl->trace[tl].level = (int32_t)level;
+                ctl->trace[tl].mode = kModeSmall;
+                ctl->trace[tl].list_size = in_cnt;
+                ctl->trace[tl].edges = E;
+                ctl->trace[tl].t_ns = (int64_t)(global_ns() - ctl->t_start);
+                ctl->trace_len = tl + 1;
+            }
+            ctl->relaxed += (unsigned long long)E;
+        }
+        par ^= 1u;
+        level += 1u;
+        in_cnt = ncnt;
+        E = nedges;
+        ++steps;
+        if (stop || in_cnt == 0 || E > lim || level >= max_levels) break;
+    }
+    // every CTA has read its last counter before CTA 0 zeroes them
+    bool stop_unused = false;
+    if (!failed && !grid_barrier(ctl, &stop_unused)) failed = true;
+    if (failed) {
+        if (threadIdx.x == 0) {
+            atomicOr(&ctl->error, kErrDeadline);
+            ctl->active = 0u;
+            if (p.use_cond) cudaGraphSetConditional(p.cond, 0u);
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) ctl->small_pack[k] = 0ull;
+        p.lists[par].scan[in_cnt] = (int32_t)E;  // sentinel (read by other strategies' kernels)
+        ctl->par = par;
+        ctl->level = level;
+        ctl->in_cnt = (uint32_t)in_cnt;
+        ctl->in_edges = (uint64_t)E;
+        ctl->out_pack = 0ull;
+        ctl->step = step0 + steps;
+        set_loop(p, ctl, in_cnt > 0);
+        __threadfence();
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -66,6 +66,9 @@ __global__ void k_prepare(StepParams p, int32_t src, uint32_t *status, int kind,
     c->sub_in = 0;
     c->hp_kind = (p.hp_threshold > 0 && (int64_t)c->in_cnt < p.hp_threshold) ? 2u : (p.hp_mode == 1 ? 3u : 1u);
     c->hp_mdt = (uint32_t)p.mdt;
+    c->small_pack[0] = c->small_pack[1] = c->small_pack[2] = 0ull;
+    c->bar_count = 0u;
+    c->bar_stop = 0u;
     c->hp_lvl = 0;
     c->hp_mdt_pending = 0;
     c->sub_maxdeg = 0ull;

@@ -38,7 +38,8 @@ class lb_options(ctypes.Structure):
     _fields_ = [("hist_bins", ctypes.c_int32), ("mdt_override", ctypes.c_int32), ("hp_threshold", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("wd_tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("hp_mode", ctypes.c_int32), ("hp_warp_max", ctypes.c_int32), ("ns_mode", ctypes.c_int32),
-                ("thread_max", ctypes.c_int32), ("hp_depth", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("thread_max", ctypes.c_int32), ("hp_depth", ctypes.c_int32), ("small_edges", ctypes.c_int32),
+                ("test_barrier_skip", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class lb_mem_stats(ctypes.Structure):
@@ -63,7 +64,7 @@ class lb_query_stats(ctypes.Structure):
 class lb_server_options(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("idle_us", ctypes.c_int32), ("mem_fraction", ctypes.c_double), ("launch_ms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class lb_server_info_t(ctypes.Structure):
@@ -342,11 +343,11 @@ def lb_bfs_wd_noalloc(offsets_dev, cols_dev, n: int, m: int, src: int, levels_de
 
 
 def lb_server_create(graphs, slots: int = 0, ctas_per_sm: int = 0, tile: int = 0, idle_us: int = 0,
-                     mem_fraction: float = 0.0, launch_ms: int = 0) -> int:
+                     mem_fraction: float = 0.0, launch_ms: int = 0, policy: int = 0) -> int:
     """Persistent multi-query engine over resident graphs (lb_graph handles)."""
     arr = (ctypes.c_void_p * len(graphs))(*graphs)
     o = lb_server_options(slots=slots, ctas_per_sm=ctas_per_sm, tile=tile, idle_us=idle_us, mem_fraction=mem_fraction,
-                          launch_ms=launch_ms)
+                          launch_ms=launch_ms, policy=policy)
     h = ctypes.c_void_p()
     _check(_load().lb_server_create(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(o), ctypes.byref(h)))
     return h.value

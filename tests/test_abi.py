@@ -48,14 +48,16 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lb_options), sizeof(lb_mem_stats), sizeof(lb_query_stats), sizeof(lb_step_record));
   printf("%zu %zu %zu %zu\n", offsetof(lb_query_stats, status), offsetof(lb_query_stats, device_ms), offsetof(lb_mem_stats, ns_split), offsetof(lb_step_record, t_ns));
   printf("%zu %zu %zu %zu\n", sizeof(lb_server_state_t), sizeof(lb_slot_state_t), offsetof(lb_server_state_t, slot), offsetof(lb_slot_state_t, ticket));
-  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max),
          offsetof(lb_options, ns_mode), offsetof(lb_options, thread_max), offsetof(lb_options, hp_depth),
-         sizeof(lb_options));
+         offsetof(lb_options, small_edges), sizeof(lb_options));
+  printf("%zu %zu %zu %zu\n", offsetof(lb_server_options, mem_fraction), offsetof(lb_server_options, launch_ms),
+         offsetof(lb_server_options, policy), sizeof(lb_server_options));
   return 0;
 }''')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
-    a, b, c, d = subprocess.check_output([str(exe)], text=True).strip().splitlines()
+    a, b, c, d, e = subprocess.check_output([str(exe)], text=True).strip().splitlines()
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(lb.lb_options), ctypes.sizeof(lb.lb_mem_stats), ctypes.sizeof(lb.lb_query_stats),
@@ -66,7 +68,11 @@ int main(void) {
                                            lb.lb_server_state_t.slot.offset, lb.lb_slot_state_t.ticket.offset]
     assert [int(x) for x in d.split()] == [lb.lb_options.hp_mode.offset, lb.lb_options.hp_warp_max.offset,
                                            lb.lb_options.ns_mode.offset, lb.lb_options.thread_max.offset,
-                                           lb.lb_options.hp_depth.offset, ctypes.sizeof(lb.lb_options)]
+                                           lb.lb_options.hp_depth.offset, lb.lb_options.small_edges.offset,
+                                           ctypes.sizeof(lb.lb_options)]
+    assert [int(x) for x in e.split()] == [lb.lb_server_options.mem_fraction.offset,
+                                           lb.lb_server_options.launch_ms.offset, lb.lb_server_options.policy.offset,
+                                           ctypes.sizeof(lb.lb_server_options)]
 
 
 def test_version_and_error_string():

@@ -381,10 +381,9 @@ def test_device_created_graph_matches():
 
 @pytest.mark.parametrize("shift", [0, 1, 2, 3])
 def test_wd_with_unaligned_column_array(shift):
-    # the WD relax bulk-prefetches long adjacency lists into L2 in 16-byte
-    # units; a caller column array at any 4-byte offset (here through the
-    # entry point that works on caller device arrays) must give the same
-    # levels as the oracle
+    # a caller column array at any 4-byte offset (through the entry point
+    # that works on caller device arrays) must give the same levels as the
+    # oracle: the walk makes no alignment assumption about it
     import torch
     g = gg.rmat(14, 16, seed=3, weights=None)
     src = gg.max_degree_vertex(g)

@@ -47,13 +47,14 @@ def make_requests(graphs, n, seed):
     return reqs
 
 
-@pytest.mark.parametrize("slots,tile", [(0, 0), (3, 256), (17, 8192)])
-def test_batch_matches_oracle(mix, slots, tile):
+@pytest.mark.parametrize("slots,tile,policy", [(0, 0, 0), (3, 256, 0), (17, 8192, 0), (0, 0, 1), (5, 1024, 1)])
+def test_batch_matches_oracle(mix, slots, tile, policy):
+    # policy 0: the oldest query's tiles first; 1: round robin only
     import torch
     graphs, handles = mix
     reqs = make_requests(graphs, 60, seed=slots + tile)
     outs = [torch.full((graphs[r.graph].n,), 7, dtype=torch.int32, device="cuda") for r in reqs]
-    S = sv.Server(handles, slots=slots, tile=tile)
+    S = sv.Server(handles, slots=slots, tile=tile, policy=policy)
     try:
         st = S.run_batch(reqs, outs, timeout_s=120)
         assert all(x == 0 for x in st), st
