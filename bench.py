@@ -437,6 +437,16 @@ def _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffer
     srv_p = sv.serve(S, pois, outs_b, timeout_s=args.serve_timeout)
     torch.cuda.synchronize()
     exact_p = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b)) and srv_p["statuses_ok"]
+    # the same arrivals with round-robin tile claiming only (policy 1)
+    S_rr = sv.Server(G, policy=1)
+    try:
+        outs_c = buffers(pois)
+        S_rr.run_batch(burst[:64], buffers(burst[:64]))
+        srv_rr = sv.serve(S_rr, pois, outs_c, timeout_s=args.serve_timeout)
+        torch.cuda.synchronize()
+        exact_p = exact_p and all(torch.equal(a, c) for a, c in zip(outs_a, outs_c)) and srv_rr["statuses_ok"]
+    finally:
+        S_rr.close()
     rate_hi = 0.8 * args.serve_queries / batched_s
     pois_hi = sv.poisson_schedule(args.serve_queries, rate_hi, [g.n for g in cg], cand, seed=2)
     outs_b = buffers(pois_hi)
@@ -455,6 +465,9 @@ def _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffer
             "poisson_rate_qps": rate,
             "one_at_a_time_latency": {k: one_p[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
             "batched_latency": {k: srv_p[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
+            "batched_latency_round_robin": {k: srv_rr[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
+            "claiming": "oldest query first, then round robin (policy 0); round robin only (policy 1) beside it",
+            "pool_bytes": info["pool_bytes"], "query_bytes_largest_graph": info["slot_bytes"],
             "batched_latency_at_0.8x_batched_capacity": {"rate_qps": rate_hi, **{k: srv_hi[k] for k in
                                                                                  ("p50_ms", "p99_ms", "qps")}},
             "exact_vs_one_at_a_time": bool(exact and exact_p and exact_hi), "slots": info["slots"],

@@ -301,15 +301,24 @@ lb_status lb_wd_offsets(const int64_t *deg, int64_t F, int64_t T, int64_t *node_
 typedef struct lb_server lb_server;
 
 typedef struct lb_server_options {
-    int32_t slots;        /* queries in flight at most; 0 = as many as fit in
-                             mem_fraction of free HBM, at most 256 */
+    int32_t slots;        /* queries in flight at most (0 = 256, at most
+                             4096); how many run at once is also bounded by
+                             the workspace pool (mem_fraction) */
     int32_t ctas_per_sm;  /* persistent grid: CTAs per SM (0 = occupancy) */
     int32_t tile;         /* largest work tile in worklist edges, 256..8192
                              (0 = 8192); a job's tiles shrink to spread it
                              over its share of the grid */
     int32_t idle_us;      /* the kernel exits after this long with no work
                              (0 = 1000); it is relaunched on demand */
-    double mem_fraction;  /* share of free HBM the slots may take (0 = 0.5) */
+    double mem_fraction;  /* share of free HBM the workspace pool may take,
+                             reserved at creation; the pool is no larger
+                             than `slots` queries on the largest graph need
+                             (0 = 0.5).  Admission by memory: a query's
+                             workspace (bitmaps and two worklists sized for
+                             its own graph) is reserved in the pool when it
+                             is admitted and returned when it completes; a
+                             query that does not fit waits, in arrival
+                             order, until completions free enough */
     int32_t launch_ms;    /* one persistent launch leaves after this long
                              (0 = 600000, ten minutes); while queries are
                              pending or in flight the next submit / poll
@@ -324,13 +333,16 @@ typedef struct lb_server_options {
 } lb_server_options;
 
 typedef struct lb_server_info_t {
-    int32_t slots;            /* slots allocated (admission by free HBM) */
+    int32_t slots;            /* queries in flight at most */
     int32_t grid;             /* CTAs of the persistent kernel */
-    int64_t slot_bytes;       /* device bytes per slot */
-    int64_t slot_n;           /* largest vertex count a slot serves */
+    int64_t slot_bytes;       /* workspace bytes of a query on the largest graph */
+    int64_t slot_n;           /* largest vertex count of a resident graph */
     int64_t kernel_launches;  /* persistent-kernel launches so far */
     int64_t submitted;
     int64_t completed;        /* completions returned by lb_server_poll */
+    int64_t pool_bytes;       /* device memory pool for query workspaces */
+    int64_t pool_free;        /* bytes of the pool not reserved now */
+    int64_t pending;          /* submitted queries waiting for pool memory */
 } lb_server_info_t;
 
 typedef struct lb_completion {

@@ -79,8 +79,10 @@ struct DeviceGuard {
 
 constexpr int kStrategies = 7;
 
+// Default small_edges.  Measured (R-MAT scale 24 BFS / 4096^2 grid BFS):
+// 65536 edges 2.12 / 65.8 ms, 16384 edges 2.12 / 58.7 ms, off 2.09 / 118 ms.
 #ifndef LB_SMALL_EDGES_DEFAULT
-#define LB_SMALL_EDGES_DEFAULT 65536
+#define LB_SMALL_EDGES_DEFAULT 16384
 #endif
 
 constexpr int32_t LB_TUNE_BOTH = 2;  // lb_autotune: time a BFS and an SSSP per source
@@ -467,11 +469,45 @@ lb_status build_exec(lb_graph *g, int s, bool sssp, cudaGraphExec_t *out) {
     p.use_cond = 1;
     p.cond = h;
     const int grid = step_grid(g, s, sssp);
-    e = cudaStreamBeginCaptureToGraph(g->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    // WD with small-list levels: the loop body starts with an IF node whose
+    // body is the persistent small-list launch; the step kernel sets its
+    // condition for the next pass (the next list has at most small_edges
+    // edges), so large levels launch nothing extra.  It runs on the first
+    // pass (default 1) and returns at once there if the list is large.
+    cudaGraphNode_t if_node = nullptr;
+    if (p.small_edges > 0) {
+        cudaGraphConditionalHandle hs;
+        e = cudaGraphConditionalHandleCreate(&hs, body, 1, cudaGraphCondAssignDefault);
+        alignas(cudaGraphNodeParams) unsigned char ip_store[sizeof(cudaGraphNodeParams)];
+        memset(ip_store, 0, sizeof(ip_store));
+        cudaGraphNodeParams &ip = *reinterpret_cast<cudaGraphNodeParams *>(ip_store);
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hs;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&if_node, body, nullptr, nullptr, 0, &ip);
+        if (e == cudaSuccess) {
+            p.use_cond_small = 1;
+            p.cond_small = hs;
+            e = cudaStreamBeginCaptureToGraph(g->stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t le = launch_small_levels(sssp, p, small_grid(g), g->stream);
+                cudaGraph_t captured = nullptr;
+                e = cudaStreamEndCapture(g->stream, &captured);
+                if (le != cudaSuccess) e = le;
+            }
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return fail(LB_ERR_CUDA, "building the small-list node failed: %s", cudaGetErrorString(e));
+        }
+    }
+    e = cudaStreamBeginCaptureToGraph(g->stream, body, if_node ? &if_node : nullptr, nullptr, if_node ? 1 : 0,
+                                      cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = cudaSuccess;
         if (hp_needs_mdt_kernel(g, s)) le = launch_hp_mdt(p, 2 * g->sms, g->stream);
-        if (le == cudaSuccess && p.small_edges > 0) le = launch_small_levels(sssp, p, small_grid(g), g->stream);
         if (le == cudaSuccess) le = launch_step(s, sssp, p, grid, g->stream);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(g->stream, &captured);

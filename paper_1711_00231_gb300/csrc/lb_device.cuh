@@ -538,6 +538,7 @@ __device__ __forceinline__ void set_loop(const StepParams &p, Ctl *ctl, bool mor
     }
     ctl->active = more ? 1u : 0u;
     if (p.use_cond) cudaGraphSetConditional(p.cond, more ? 1u : 0u);
+    if (p.use_cond_small) cudaGraphSetConditional(p.cond_small, (more && ctl->in_edges <= (uint64_t)p.small_edges) ? 1u : 0u);
 }
 
 // Finalise a plain (non-HP) step: the output list becomes the input list.

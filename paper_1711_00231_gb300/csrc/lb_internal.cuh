@@ -149,6 +149,9 @@ struct StepParams {
     int32_t use_cond;
     int32_t small_edges;   // WD: lists of at most this many edges run in the persistent small-list kernel (0: off)
     cudaGraphConditionalHandle cond;
+    cudaGraphConditionalHandle cond_small;  // device loop: run the small-list kernel on the next pass
+    int32_t use_cond_small;
+    int32_t pad2;
 };
 
 // ---- launch entry points implemented by the strategy translation units --

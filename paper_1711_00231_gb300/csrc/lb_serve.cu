@@ -27,9 +27,12 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "lb_steps.cuh"
@@ -87,7 +90,46 @@ struct Req {
     int32_t pad;
     unsigned long long out;
     unsigned long long ticket;
+    unsigned long long ws;  // the query's workspace in the pool (reserved by the host)
 };
+
+// A query's workspace (one block of the server's device pool, reserved by
+// the host before the request enters the ring): the visited / queued
+// bitmap halves and two worklists sized for its own graph (n vertices, m
+// edges), each piece 256-byte aligned.
+struct WsLayout {
+    int64_t bmw;       // words per bitmap half (a multiple of 4)
+    int64_t cap;       // worklist entries
+    int64_t tcap;      // tile-start entries per list
+    uint64_t list0;    // byte offset of list 0 (list 1 follows at list0 + list_bytes)
+    uint64_t v, beg, scan, tstart;  // byte offsets inside a list
+    uint64_t list_bytes;
+    uint64_t total;
+};
+__host__ __device__ constexpr uint64_t al256(uint64_t x) { return (x + 255u) & ~(uint64_t)255u; }
+__host__ __device__ inline WsLayout ws_layout(int64_t n, int64_t m) {
+    WsLayout L;
+    L.bmw = ((n + 31) / 32 + 3) / 4 * 4;
+    L.cap = n;
+    L.tcap = m / kTileGrain + 2;
+    L.list0 = al256(8u * (uint64_t)L.bmw);
+    L.v = 0;
+    L.beg = al256(4u * (uint64_t)L.cap);
+    L.scan = L.beg + al256(4u * (uint64_t)L.cap);
+    L.tstart = L.scan + al256(4u * (uint64_t)(L.cap + 1));
+    L.list_bytes = L.tstart + al256(4u * (uint64_t)L.tcap);
+    L.total = L.list0 + 2u * L.list_bytes;
+    return L;
+}
+__host__ __device__ inline NodeList ws_list(unsigned char *ws, const WsLayout &L, uint32_t b) {
+    unsigned char *base = ws + L.list0 + (uint64_t)b * L.list_bytes;
+    NodeList l;
+    l.v = (int32_t *)(base + L.v);
+    l.beg = (int32_t *)(base + L.beg);
+    l.scan = (int32_t *)(base + L.scan);
+    l.tstart = (int32_t *)(base + L.tstart);
+    return l;
+}
 
 struct Done {
     unsigned long long ticket;
@@ -146,8 +188,7 @@ struct Slot {
     unsigned long long ticket;
     unsigned long long t_admit;
     uint32_t *status;
-    uint32_t *bitmap;  // 2 x Params::bm_words: BFS visited bits / SSSP queued bits (even, odd iterations)
-    NodeList lists[2];
+    unsigned char *ws;  // the query's workspace (ws_layout of its graph): set at admission
 };
 
 struct Shared {  // device-global control of the persistent kernel
@@ -179,10 +220,6 @@ struct Params {
     Shared *sh;
     int32_t tile;
     int32_t policy;     // 0: the oldest query's tiles first, then round robin; 1: round robin
-    int64_t slot_cap;   // worklist entries per slot list
-    int64_t tile_cap;   // tile starts per slot list
-    int64_t slot_n;     // largest n a slot serves
-    int64_t bm_words;   // words per half of a slot's bitmap (a multiple of 4)
     uint64_t idle_ns;
     uint64_t hard_ns;
 };
@@ -254,6 +291,7 @@ struct SlotState {
     uint32_t level, par, in_cnt;
     uint64_t in_edges;
     uint32_t *status;
+    unsigned char *ws;
 };
 
 __device__ __forceinline__ SlotState slot_state(const Slot *S) {
@@ -267,6 +305,7 @@ __device__ __forceinline__ SlotState slot_state(const Slot *S) {
     t.in_cnt = V->in_cnt;
     t.in_edges = V->in_edges;
     t.status = V->status;
+    t.ws = V->ws;
     return t;
 }
 
@@ -335,13 +374,14 @@ __device__ bool finish_job(const Params &P, Slot *S, uint32_t kind) {
             complete_query(P, S, LB_OK);
             return false;
         }
-        NodeList L = S->lists[0];
+        const WsLayout W = ws_layout(g.n, g.m);
+        NodeList L = ws_list(st.ws, W, 0);
         L.v[0] = st.src;
         L.beg[0] = (int32_t)beg;
         L.scan[0] = 0;
         L.scan[1] = (int32_t)deg;
         const int64_t grains = (deg + kTileGrain - 1) / kTileGrain;
-        for (int64_t k = 0; k < grains && k < P.tile_cap; ++k) L.tstart[k] = 0;
+        for (int64_t k = 0; k < grains && k < W.tcap; ++k) L.tstart[k] = 0;
         S->in_cnt = 1;
         S->in_edges = (uint64_t)deg;
         const int64_t Tj = job_tile(P, deg);
@@ -352,13 +392,14 @@ __device__ bool finish_job(const Params &P, Slot *S, uint32_t kind) {
         const unsigned long long pk = ld_volatile(&S->out_pack);
         int64_t cnt = (int64_t)(pk >> 32);
         const int64_t edges = (int64_t)(pk & 0xFFFFFFFFull);
-        if (cnt > P.slot_cap) { atomicOr(&S->error, kErrCapacity); cnt = P.slot_cap; }
+        const WsLayout W = ws_layout(g.n, g.m);
+        if (cnt > W.cap) { atomicOr(&S->error, kErrCapacity); cnt = W.cap; }
         S->relaxed = ld_volatile(&S->relaxed) + st.in_edges;
         S->level = st.level + 1;
         const uint32_t out = st.par ^ 1u;
         const uint32_t err = atomicOr(&S->error, 0u);
         if (cnt > 0 && st.level + 1 <= (uint32_t)g.n && !(err & (kErrCapacity | kErrBounds))) {
-            S->lists[out].scan[cnt] = (int32_t)edges;
+            ws_list(st.ws, W, out).scan[cnt] = (int32_t)edges;
             S->par = out;
             S->in_cnt = (uint32_t)cnt;
             S->in_edges = (uint64_t)edges;
@@ -392,10 +433,12 @@ __device__ void init_tile(const Params &P, Slot *S, int64_t k) {
     for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) status[i] = i == src ? 0u : kInf;
     // BFS: this chunk's visited bits; SSSP: its queued bits in both halves
     // (kInitChunk is a multiple of 32, so chunks own whole words)
+    const WsLayout W = ws_layout(g.n, g.m);
+    uint32_t *bitmap = (uint32_t *)st.ws;
     const int64_t w0 = v0 / 32, w1 = (v1 + 31) / 32;
     for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-        S->bitmap[w] = (!sssp && w == (src >> 5)) ? (1u << (src & 31)) : 0u;
-        if (sssp) S->bitmap[P.bm_words + w] = 0u;
+        bitmap[w] = (!sssp && w == (src >> 5)) ? (1u << (src & 31)) : 0u;
+        if (sssp) bitmap[W.bmw + w] = 0u;
     }
 }
 
@@ -413,7 +456,9 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, 
                            WarpScratch &ws) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
-    uint32_t *qcur = queued_half(S->bitmap, P.bm_words, st.level);
+    const WsLayout W = ws_layout(g.n, g.m);
+    uint32_t *bitmap = (uint32_t *)st.ws;
+    uint32_t *qcur = queued_half(bitmap, W.bmw, st.level);
     if (SSSP) {
         // The other half still holds the bits of the previous iteration,
         // whose queued vertices are exactly this iteration's list entries
@@ -421,29 +466,29 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, 
         // bit is harmless, as such a vertex is never listed or expanded).
         // Tile t clears the bits of its share of the entries for the next
         // iteration, which starts only after every tile of this one.
-        uint32_t *qn = queued_half(S->bitmap, P.bm_words, st.level + 1u);
+        uint32_t *qn = queued_half(bitmap, W.bmw, st.level + 1u);
         const int64_t per = ((int64_t)st.in_cnt + ntiles - 1) / ntiles;
         const int64_t k0 = t * per, k1 = min(k0 + per, (int64_t)st.in_cnt);
-        const int32_t *vin = S->lists[st.par].v;
+        const int32_t *vin = ws_list(st.ws, W, st.par).v;
         for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             const int32_t u = __ldcg(vin + k);
             if (u >= 0 && (int64_t)u < g.n) atomicAnd(&qn[(uint32_t)u >> 5], ~(1u << ((uint32_t)u & 31u)));
         }
     }
     FlushOut o;
-    o.list = S->lists[st.par ^ 1u];
+    o.list = ws_list(st.ws, W, st.par ^ 1u);
     o.elist = nullptr;
     o.pack = &S->out_pack;
-    o.cap = P.slot_cap;
-    o.tile_cap = P.tile_cap;
+    o.cap = W.cap;
+    o.tile_cap = W.tcap;
     o.tile = (int32_t)kTileGrain;
     o.mdt = 1;
     o.err = &S->error;
     o.pushes = &S->pushes;
     o.child_first = nullptr;
     uint32_t cnt = 0;
-    wd_walk_tile<SSSP, kItems, true>(g, S->lists[st.par], st.in_cnt, (int64_t)st.in_edges, q * kTileGrain, t,
-                                     S->bitmap, qcur, st.status, st.level, &S->error, wb, ws, cnt, o);
+    wd_walk_tile<SSSP, kItems, true>(g, ws_list(st.ws, W, st.par), st.in_cnt, (int64_t)st.in_edges, q * kTileGrain,
+                                     t, bitmap, qcur, st.status, st.level, &S->error, wb, ws, cnt, o);
 #if LB_BLOCK_FLUSH
     wflush_block<kOutNode, true>(wb, ws, cnt, o);
 #else
@@ -473,7 +518,9 @@ __device__ void admit(const Params &P) {
         r.kind = vr->kind;
         r.out = vr->out;
         r.ticket = vr->ticket;
+        r.ws = vr->ws;
         S->ticket = r.ticket;
+        S->ws = reinterpret_cast<unsigned char *>(r.ws);
         S->graph = r.graph;
         S->src = r.src;
         S->kind = r.kind;
@@ -487,7 +534,7 @@ __device__ void admit(const Params &P) {
         bool valid = r.graph >= 0 && r.graph < P.ngraphs && r.out != 0ull && (r.kind == 0 || r.kind == 1);
         if (valid) {
             const GraphDev g = P.graphs[r.graph];
-            valid = r.src >= 0 && (int64_t)r.src < g.n && g.n <= P.slot_n && (r.kind == 0 || g.w != nullptr);
+            valid = r.src >= 0 && (int64_t)r.src < g.n && r.ws != 0ull && (r.kind == 0 || g.w != nullptr);
         }
         S->busy = 1;
         atomicAdd(&sh->active, 1u);
@@ -808,18 +855,30 @@ struct lb_server {
     std::mutex mu;
     lb_server_options opt{};
     std::vector<lb_graph *> graphs;
-    std::vector<int64_t> graph_n;
+    std::vector<int64_t> graph_n, graph_m;
     std::vector<bool> graph_weighted;
     GraphDev *d_graphs = nullptr;
     Slot *d_slots = nullptr;
     Shared *d_shared = nullptr;
     HostShared *h_ring = nullptr;  // pinned, mapped
     HostShared *d_ring = nullptr;  // device view
-    std::vector<void *> bufs;      // slot workspace allocations
     int32_t nslots = 0;
-    int64_t slot_n = 0, slot_m = 0, slot_cap = 0, tile_cap = 0;
-    int64_t bm_words = 0;  // words per half of a slot's bitmap
-    int64_t slot_bytes = 0;
+    int64_t slot_n = 0;            // largest vertex count of a resident graph
+    int64_t slot_bytes = 0;        // workspace bytes of a query on the largest graph
+    // Admission by device memory: every query's workspace is a block of
+    // this pool, reserved on the host (first fit, free neighbours merged)
+    // before its request enters the device ring; a request that does not
+    // fit waits in `pending` (arrival order) until completions free memory.
+    unsigned char *pool = nullptr;
+    uint64_t pool_bytes = 0, pool_free = 0;
+    std::map<uint64_t, uint64_t> free_ranges;  // offset -> bytes
+    std::unordered_map<unsigned long long, std::pair<uint64_t, uint64_t>> held;  // ticket -> (offset, bytes)
+    struct Pending {
+        int32_t graph, src, kind;
+        unsigned long long out, ticket;
+        uint64_t bytes;
+    };
+    std::deque<Pending> pending;
     int grid = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_kernel = nullptr;
@@ -847,6 +906,66 @@ lb_status sfail(lb_status s, const char *msg, cudaError_t e = cudaSuccess) {
             return sfail(e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, what, e_); \
     } while (0)
 
+// First fit in the pool; every block is a multiple of 256 bytes.
+bool pool_alloc(lb_server *s, uint64_t bytes, uint64_t *off) {
+    for (auto it = s->free_ranges.begin(); it != s->free_ranges.end(); ++it) {
+        if (it->second < bytes) continue;
+        *off = it->first;
+        const uint64_t rest = it->second - bytes, at = it->first + bytes;
+        s->free_ranges.erase(it);
+        if (rest) s->free_ranges[at] = rest;
+        s->pool_free -= bytes;
+        return true;
+    }
+    return false;
+}
+
+void pool_release(lb_server *s, uint64_t off, uint64_t bytes) {
+    auto it = s->free_ranges.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != s->free_ranges.end() && it->first + it->second == nx->first) {  // merge with the next range
+        it->second += nx->second;
+        s->free_ranges.erase(nx);
+    }
+    if (it != s->free_ranges.begin()) {  // and with the previous one
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            s->free_ranges.erase(it);
+        }
+    }
+    s->pool_free += bytes;
+}
+
+uint64_t query_bytes(const lb_server *s, int32_t graph) {
+    const WsLayout L = ws_layout(s->graph_n[(size_t)graph], s->graph_m[(size_t)graph]);
+    return al256(L.total);
+}
+
+// Moves pending requests, in arrival order, into the device ring while
+// their workspaces fit in the pool (the first that does not fit waits, so
+// a large query is not overtaken forever by smaller ones).
+void pump(lb_server *s) {
+    bool moved = false;
+    while (!s->pending.empty() && s->submitted - s->acked < kRing) {
+        const lb_server::Pending &q = s->pending.front();
+        uint64_t off = 0;
+        if (!pool_alloc(s, q.bytes, &off)) break;
+        Req &r = s->h_ring->req[s->submitted % kRing];
+        r.graph = q.graph;
+        r.src = q.src;
+        r.kind = q.kind;
+        r.out = q.out;
+        r.ticket = q.ticket;
+        r.ws = (unsigned long long)(uintptr_t)(s->pool + off);
+        s->held[q.ticket] = {off, q.bytes};
+        s->submitted++;
+        s->pending.pop_front();
+        moved = true;
+    }
+    if (moved) __atomic_store_n(&s->h_ring->submitted, s->submitted, __ATOMIC_RELEASE);
+}
+
 void destroy_server(lb_server *s) {
     if (!s) return;
     int prev = -1;
@@ -856,7 +975,7 @@ void destroy_server(lb_server *s) {
         __atomic_store_n(&s->h_ring->stop, 1u, __ATOMIC_RELEASE);
     }
     if (s->stream) cudaStreamSynchronize(s->stream);
-    for (void *p : s->bufs) cudaFree(p);
+    if (s->pool) cudaFree(s->pool);
     if (s->d_graphs) cudaFree(s->d_graphs);
     if (s->d_slots) cudaFree(s->d_slots);
     if (s->d_shared) cudaFree(s->d_shared);
@@ -886,10 +1005,6 @@ lb_status launch_kernel(lb_server *s) {
     P.sh = s->d_shared;
     P.tile = s->opt.tile;
     P.policy = s->opt.policy;
-    P.slot_cap = s->slot_cap;
-    P.tile_cap = s->tile_cap;
-    P.slot_n = s->slot_n;
-    P.bm_words = s->bm_words;
     P.idle_ns = (uint64_t)s->opt.idle_us * 1000ull;
     P.hard_ns = (uint64_t)s->opt.launch_ms * 1000000ull;  // one persistent launch never outlives this
     k_serve_t0<<<1, 1, 0, s->stream>>>(s->d_shared);
@@ -962,26 +1077,24 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
         gd.push_back(d);
         s->graphs.push_back(g);
         s->graph_n.push_back(n);
+        s->graph_m.push_back(m);
         s->graph_weighted.push_back(wgt != 0);
         if (n > s->slot_n) s->slot_n = n;
-        if (m > s->slot_m) s->slot_m = m;
     }
-    s->slot_cap = s->slot_n;
-    s->tile_cap = s->slot_m / kTileGrain + 2;
-    // per slot: two bitmaps + two worklists (v, beg, scan, tile starts)
-    s->bm_words = ((s->slot_n + 31) / 32 + 3) / 4 * 4;
-    const int64_t per_list = 4 * s->slot_cap + 4 * s->slot_cap + 4 * (s->slot_cap + 1) + 4 * s->tile_cap;
-    s->slot_bytes = 4 * 2 * s->bm_words + 2 * per_list + 4096;
+    // the workspace pool: mem_fraction of free HBM, but no more than every
+    // slot holding a query on the largest graph needs
+    for (int32_t i = 0; i < ngraphs; ++i)
+        if ((int64_t)query_bytes(s, i) > s->slot_bytes) s->slot_bytes = (int64_t)query_bytes(s, i);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    int64_t fit = (int64_t)((double)free_b * o.mem_fraction) / (s->slot_bytes > 0 ? s->slot_bytes : 1);
-    int32_t want = o.slots > 0 ? o.slots : 256;
-    if (fit < want) want = (int32_t)fit;
-    if (want < 1) {
+    s->nslots = o.slots > 0 ? o.slots : 256;
+    const uint64_t budget = (uint64_t)((double)free_b * o.mem_fraction) & ~(uint64_t)255u;
+    const uint64_t need = (uint64_t)s->slot_bytes * (uint64_t)s->nslots;
+    s->pool_bytes = budget < need ? budget : need;
+    if (s->pool_bytes < (uint64_t)s->slot_bytes) {
         destroy_server(s);
-        return sfail(LB_ERR_OOM, "not enough free device memory for one query slot");
+        return sfail(LB_ERR_OOM, "not enough free device memory for one query on the largest graph");
     }
-    s->nslots = want;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, kBlock, 0);
     if (occ < 1) occ = 1;
@@ -994,28 +1107,18 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
         memset(s->h_ring, 0, sizeof(HostShared));
         e = cudaHostGetDevicePointer((void **)&s->d_ring, s->h_ring, 0);
     }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->pool, (size_t)s->pool_bytes);
+    if (e == cudaSuccess) {
+        s->free_ranges[0] = s->pool_bytes;
+        s->pool_free = s->pool_bytes;
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_graphs, sizeof(GraphDev) * gd.size());
     if (e == cudaSuccess) e = cudaMemcpy(s->d_graphs, gd.data(), sizeof(GraphDev) * gd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_shared, sizeof(Shared));
     if (e == cudaSuccess) e = cudaMemset(s->d_shared, 0, sizeof(Shared));
     if (e == cudaSuccess) e = cudaMemset(&s->d_shared->oldest, 0xFF, sizeof(unsigned long long));  // kNoOldest
     std::vector<Slot> hs((size_t)s->nslots);
-    for (int32_t i = 0; i < s->nslots && e == cudaSuccess; ++i) {
-        Slot &S = hs[(size_t)i];
-        memset(&S, 0, sizeof(Slot));
-        auto get = [&](void **p, size_t bytes) {
-            if (e != cudaSuccess) return;
-            e = cudaMalloc(p, bytes);
-            if (e == cudaSuccess) s->bufs.push_back(*p);
-        };
-        get((void **)&S.bitmap, 4 * 2 * (size_t)s->bm_words);
-        for (int b = 0; b < 2; ++b) {
-            get((void **)&S.lists[b].v, 4 * (size_t)s->slot_cap);
-            get((void **)&S.lists[b].beg, 4 * (size_t)s->slot_cap);
-            get((void **)&S.lists[b].scan, 4 * (size_t)(s->slot_cap + 1));
-            get((void **)&S.lists[b].tstart, 4 * (size_t)s->tile_cap);
-        }
-    }
+    for (Slot &S : hs) memset(&S, 0, sizeof(Slot));
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_slots, sizeof(Slot) * (size_t)s->nslots);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_slots, hs.data(), sizeof(Slot) * (size_t)s->nslots, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -1040,8 +1143,11 @@ lb_status lb_server_info(const lb_server *s, lb_server_info_t *info) {
     info->slot_bytes = s->slot_bytes;
     info->slot_n = s->slot_n;
     info->kernel_launches = (int64_t)s->launches;
-    info->submitted = (int64_t)s->submitted;
+    info->submitted = (int64_t)(s->submitted + s->pending.size());
     info->completed = (int64_t)s->acked;
+    info->pool_bytes = (int64_t)s->pool_bytes;
+    info->pool_free = (int64_t)s->pool_free;
+    info->pending = (int64_t)s->pending.size();
     return LB_OK;
 }
 
@@ -1052,19 +1158,23 @@ lb_status lb_server_submit(lb_server *s, int32_t graph, int32_t src, int32_t kin
     if (kind != LB_KIND_BFS && kind != LB_KIND_SSSP) return sfail(LB_ERR_ARG, "kind must be LB_KIND_BFS or LB_KIND_SSSP");
     if (kind == LB_KIND_SSSP && !s->graph_weighted[(size_t)graph]) return sfail(LB_ERR_UNSUPPORTED, "SSSP needs a weighted graph");
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->submitted - s->acked >= kRing) return sfail(LB_ERR_UNSUPPORTED, "request ring full: poll completions first");
+    if (s->submitted - s->acked + s->pending.size() >= kRing)
+        return sfail(LB_ERR_UNSUPPORTED, "request ring full: poll completions first");
+    const uint64_t bytes = query_bytes(s, graph);
+    if (bytes > s->pool_bytes) return sfail(LB_ERR_OOM, "the query needs more device memory than the server's pool");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != s->device) cudaSetDevice(s->device);
-    Req &r = s->h_ring->req[s->submitted % kRing];
-    r.graph = graph;
-    r.src = src;
-    r.kind = kind;
-    r.out = (unsigned long long)(uintptr_t)out_dev;
-    r.ticket = s->next_ticket++;
-    if (ticket) *ticket = r.ticket;
-    s->submitted++;
-    __atomic_store_n(&s->h_ring->submitted, s->submitted, __ATOMIC_RELEASE);
+    lb_server::Pending q;
+    q.graph = graph;
+    q.src = src;
+    q.kind = kind;
+    q.out = (unsigned long long)(uintptr_t)out_dev;
+    q.ticket = s->next_ticket++;
+    q.bytes = bytes;
+    if (ticket) *ticket = q.ticket;
+    s->pending.push_back(q);
+    pump(s);  // admitted to the device once its workspace fits in the pool
     lb_status st = ensure_running(s);
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     return st;
@@ -1087,10 +1197,16 @@ lb_status lb_server_poll(lb_server *s, lb_completion *out, int32_t cap, int32_t 
         out[k].iterations = d.iterations;
         out[k].edges_relaxed = (int64_t)d.edges_relaxed;
         out[k].device_ns = (int64_t)(d.t_done_ns - d.t_admit_ns);
+        auto h = s->held.find(d.ticket);  // the query's workspace returns to the pool
+        if (h != s->held.end()) {
+            pool_release(s, h->second.first, h->second.second);
+            s->held.erase(h);
+        }
         ++k;
         s->acked++;
     }
     *ndone = k;
+    pump(s);
     lb_status st = ensure_running(s);
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     return st;

@@ -70,7 +70,8 @@ class lb_server_options(ctypes.Structure):
 class lb_server_info_t(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("grid", ctypes.c_int32), ("slot_bytes", ctypes.c_int64),
                 ("slot_n", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("submitted", ctypes.c_int64),
-                ("completed", ctypes.c_int64)]
+                ("completed", ctypes.c_int64), ("pool_bytes", ctypes.c_int64), ("pool_free", ctypes.c_int64),
+                ("pending", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -51,8 +51,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max),
          offsetof(lb_options, ns_mode), offsetof(lb_options, thread_max), offsetof(lb_options, hp_depth),
          offsetof(lb_options, small_edges), sizeof(lb_options));
-  printf("%zu %zu %zu %zu\n", offsetof(lb_server_options, mem_fraction), offsetof(lb_server_options, launch_ms),
-         offsetof(lb_server_options, policy), sizeof(lb_server_options));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(lb_server_options, mem_fraction), offsetof(lb_server_options, launch_ms),
+         offsetof(lb_server_options, policy), sizeof(lb_server_options), offsetof(lb_server_info_t, pending),
+         sizeof(lb_server_info_t));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -72,7 +73,8 @@ int main(void) {
                                            ctypes.sizeof(lb.lb_options)]
     assert [int(x) for x in e.split()] == [lb.lb_server_options.mem_fraction.offset,
                                            lb.lb_server_options.launch_ms.offset, lb.lb_server_options.policy.offset,
-                                           ctypes.sizeof(lb.lb_server_options)]
+                                           ctypes.sizeof(lb.lb_server_options), lb.lb_server_info_t.pending.offset,
+                                           ctypes.sizeof(lb.lb_server_info_t)]
 
 
 def test_version_and_error_string():

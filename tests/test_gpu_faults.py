@@ -121,11 +121,13 @@ def test_server_admission_by_free_memory_refuses_when_nothing_fits():
         with pytest.raises(lb.LbError) as ei:
             sv.Server([G], mem_fraction=1e-9)
         assert ei.value.status == lb.LB_ERR_OOM
-        S = sv.Server([G], slots=4096, mem_fraction=0.001)   # as many slots as 0.1% of free HBM holds
+        S = sv.Server([G], slots=4096, mem_fraction=0.001)   # a pool of 0.1% of free HBM
         try:
             info = S.info()
-            assert 1 <= info["slots"] < 4096
-            assert info["slots"] * info["slot_bytes"] <= 0.001 * 300e9
+            assert info["slots"] == 4096
+            assert info["slot_bytes"] <= info["pool_bytes"] <= 0.001 * 300e9
+            assert info["pool_bytes"] < 4096 * info["slot_bytes"]   # memory, not the slot count, bounds admission
+            assert info["pool_free"] == info["pool_bytes"] and info["pending"] == 0
         finally:
             S.close()
     finally:

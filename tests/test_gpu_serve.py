@@ -208,3 +208,51 @@ def test_overflow_and_invalid_requests(mix):
     finally:
         S.close()
         G.close()
+
+
+def test_admission_by_memory_queues_what_does_not_fit():
+    # a pool that holds about two workspaces of the large graph: queries
+    # on it wait (pending) until completions return memory, the small
+    # graph's queries fill the rest, every result is exact and the whole
+    # pool is free at the end
+    import torch
+    big = gg.grid(512, 512, seed=6)
+    small = gg.rmat(11, 8, seed=7)
+    graphs = [big, small]
+    handles = [lb.Graph.from_csr(g) for g in graphs]
+    try:
+        probe = sv.Server(handles)
+        ws_big = probe.info()["slot_bytes"]
+        probe.close()
+        free, _ = torch.cuda.mem_get_info()
+        S = sv.Server(handles, slots=64, mem_fraction=2.5 * ws_big / free)
+        try:
+            info = S.info()
+            assert 2 * ws_big <= info["pool_bytes"] < 3 * ws_big
+            rng = np.random.default_rng(3)
+            reqs = [sv.Request(0.0, i % 2, int(rng.integers(0, graphs[i % 2].n)), "sssp" if i % 3 else "bfs")
+                    for i in range(24)]
+            outs = [torch.full((graphs[r.graph].n,), 7, dtype=torch.int32, device="cuda") for r in reqs]
+            tick = {S.submit(r.graph, r.src, r.kind, o): i for i, (r, o) in enumerate(zip(reqs, outs))}
+            saw_pending = S.info()["pending"] > 0
+            left, t_end = len(reqs), time.perf_counter() + 120
+            while left:
+                for c in S.poll():
+                    assert c[1] == 0
+                    tick.pop(c[0])
+                    left -= 1
+                inf = S.info()
+                saw_pending = saw_pending or inf["pending"] > 0
+                assert 0 <= inf["pool_free"] <= inf["pool_bytes"]
+                assert time.perf_counter() < t_end, S.state()
+            assert saw_pending
+            info = S.info()
+            assert info["pool_free"] == info["pool_bytes"] and info["pending"] == 0
+            torch.cuda.synchronize()
+            for r, o in zip(reqs, outs):
+                assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src)), r
+        finally:
+            S.close()
+    finally:
+        for h in handles:
+            h.close()
