@@ -471,13 +471,13 @@ lb_status build_exec(lb_graph *g, int s, bool sssp, cudaGraphExec_t *out) {
     const int grid = step_grid(g, s, sssp);
     // WD with small-list levels: the loop body starts with an IF node whose
     // body is the persistent small-list launch; the step kernel sets its
-    // condition for the next pass (the next list has at most small_edges
-    // edges), so large levels launch nothing extra.  It runs on the first
-    // pass (default 1) and returns at once there if the list is large.
+    // condition for the next pass (the last kSmallAfter lists had at most
+    // small_edges edges), so other levels launch nothing extra.  Off on the
+    // first pass (default 0).
     cudaGraphNode_t if_node = nullptr;
     if (p.small_edges > 0) {
         cudaGraphConditionalHandle hs;
-        e = cudaGraphConditionalHandleCreate(&hs, body, 1, cudaGraphCondAssignDefault);
+        e = cudaGraphConditionalHandleCreate(&hs, body, 0, cudaGraphCondAssignDefault);
         alignas(cudaGraphNodeParams) unsigned char ip_store[sizeof(cudaGraphNodeParams)];
         memset(ip_store, 0, sizeof(ip_store));
         cudaGraphNodeParams &ip = *reinterpret_cast<cudaGraphNodeParams *>(ip_store);

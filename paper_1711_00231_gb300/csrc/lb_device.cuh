@@ -25,7 +25,13 @@
 
 namespace lbk {
 
-constexpr int kWB = 128;  // entries per warp push buffer (multiple of 32)
+// Entries per warp push buffer (a multiple of 32).  192 measured 23% slower
+// (BFS) at R-MAT scale 24: the larger shared-memory footprint costs
+// resident CTAs.
+#ifndef LB_KWB
+#define LB_KWB 128
+#endif
+constexpr int kWB = LB_KWB;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // what a flush writes
@@ -53,6 +59,12 @@ struct FlushOut {
     int64_t tile_cap;  // tstart entries
     int32_t tile;      // edges between recorded tile starts (kTileGrain in the hot path)
     int32_t mdt;
+    // deferred offsets (kOutNode): the pushes buffered only the vertex, and
+    // the flush loads every buffered vertex's first edge and degree from
+    // `off` (all entries at once, so one latency per flush instead of one per
+    // relax group) and drops vertices without out-edges
+    const int64_t *off = nullptr;
+    int32_t defer = 0;
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -117,15 +129,26 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, ui
 // position / edge prefix `old` (packed entries << 32 | edges) reserved for
 // them.
 template <int KIND>
-__device__ __forceinline__ void wflush_prefix(const WarpBuf &b, WarpScratch &s, uint32_t cnt, const FlushOut &o,
+__device__ __forceinline__ void wflush_prefix(WarpBuf &b, WarpScratch &s, uint32_t cnt, const FlushOut &o,
                                               uint32_t &run_u, uint32_t &run_e) {
     const uint32_t lane = lane_id();
     run_u = 0;
     run_e = 0;
+    if (KIND == kOutNode && o.defer) {
+        // offsets are < m < 2^31 (checked when the graph is created)
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            const int32_t v = b.v[i];
+            const int32_t b0 = (int32_t)__ldg(o.off + v);
+            b.beg[i] = b0;
+            b.deg[i] = (uint32_t)((int32_t)__ldg(o.off + v + 1) - b0);
+        }
+        __syncwarp();
+    }
     for (uint32_t c = 0; c < cnt; c += 32) {
         const uint32_t i = c + lane;
         const uint32_t d = i < cnt ? b.deg[i] : 0u;
-        const uint32_t u = i < cnt ? out_units<KIND>(d, o.mdt) : 0u;
+        // with deferred offsets a buffered node without out-edges is dropped
+        const uint32_t u = (i < cnt && !(KIND == kOutNode && o.defer && d == 0u)) ? out_units<KIND>(d, o.mdt) : 0u;
         uint32_t iu = u, ie = d;
 #pragma unroll
         for (int k = 1; k < 32; k <<= 1) {
@@ -153,15 +176,21 @@ __device__ __forceinline__ void wflush_write(const WarpBuf &b, const WarpScratch
     }
     if (KIND == kOutNode) {
         for (uint32_t i = lane; i < cnt; i += 32) {
-            const int64_t pos = ubase + i;
+            if (o.defer && b.deg[i] == 0u) continue;  // deferred offsets: a node without out-edges
+            const int64_t pos = ubase + s.pu[i];
             const int64_t S = ebase + s.pe[i];
             o.list.v[pos] = b.v[i];
             o.list.beg[pos] = b.beg[i];
             o.list.scan[pos] = (int32_t)S;
             if (TILED) {
                 const int64_t E = S + b.deg[i];
-                for (int64_t k = (S + o.tile - 1) / o.tile; k * o.tile < E; ++k)
-                    if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+                if (o.tile == (int32_t)kTileGrain) {  // the hot path: shifts, no division
+                    for (int64_t k = (S + kTileGrain - 1) >> 8; (k << 8) < E; ++k)
+                        if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+                } else {
+                    for (int64_t k = (S + o.tile - 1) / o.tile; k * o.tile < E; ++k)
+                        if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+                }
             }
         }
     } else {
@@ -316,7 +345,14 @@ __device__ __forceinline__ uint32_t ld_mut(const uint32_t *p) {
     return COH ? __ldcg(p) : *p;
 }
 
+// Warp-uniform early exits in relax_items: after the checks when no lane
+// has a candidate, after the atomics when no lane won one.  Measured on
+// R-MAT scale 24: SSSP 8.98 -> 8.53 ms per query.
+#ifndef LB_EARLY_EXIT
+#define LB_EARLY_EXIT 1
+#endif
 // FLUSH = false: the caller flushes; then cnt + 32 * ITEMS <= kWB on entry.
+// With FlushOut::defer set (kOutNode) only the vertex is buffered.
 template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false, bool FLUSH = true>
 __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32_t (&vv)[ITEMS],
                                             const uint32_t (&ww)[ITEMS], const uint32_t (&dd)[ITEMS],
@@ -341,6 +377,12 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
         } else {
             cand[it] = !(ld_mut<COH || LB_BFS_BITMAP_CG>(bitmap + ((uint32_t)vv[it] >> 5)) & (1u << ((uint32_t)vv[it] & 31u)));
         }
+    }
+    if (LB_EARLY_EXIT) {
+        bool any = false;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) any = any || cand[it];
+        if (!__any_sync(kFull, any)) return;
     }
     uint32_t prev[ITEMS];
 #pragma unroll
@@ -372,6 +414,21 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it)
             if (won[it] && (prev[it] & (1u << ((uint32_t)vv[it] & 31u)))) won[it] = false;
+    }
+    if (LB_EARLY_EXIT) {
+        bool any = false;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) any = any || won[it];
+        if (!__any_sync(kFull, any)) return;
+    }
+    if (KIND == kOutNode && o.defer) {
+        // deferred offsets: buffer the vertex only (the flush loads its offsets)
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            wpush(wb, cnt, won[it], vv[it], 0, 0u);
+            if (FLUSH && cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
+        }
+        return;
     }
     // offsets are < m < 2^31 (checked when the graph is created)
     int32_t vb[ITEMS], ve[ITEMS];
@@ -409,6 +466,13 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
 #ifndef LB_LEAN_PUSH_SIMPLE
 #define LB_LEAN_PUSH_SIMPLE 0
 #endif
+// Pushes of the WD walk buffer only the vertex; the flush loads the offsets
+// (FlushOut::defer).  Measured on R-MAT scale 24: BFS 2.10 -> 1.92 ms, SSSP
+// 9.35 -> 9.01 ms per query (the offset loads leave each relax group's chain
+// of dependent memory accesses, and the walk needs fewer registers).
+#ifndef LB_DEFER_OFFSETS
+#define LB_DEFER_OFFSETS 1
+#endif
 // BFS relax of R loaded edges per lane with warp-uniform early exits: the
 // visited check for every item, then (only if some lane of the warp found
 // an unvisited vertex) the claims, then (only if some lane won one) the
@@ -437,6 +501,27 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
         }
     }
     if (!__any_sync(kFull, won != 0u)) return;
+    if (o.defer) {
+        // level writes, then every won vertex is buffered; the flush loads
+        // the offsets and drops vertices without out-edges
+        unsigned bal[R];
+        uint32_t tot = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((won >> r) & 1u) status[vv[r]] = level + 1;
+            bal[r] = __ballot_sync(kFull, (won >> r) & 1u);
+            tot += __popc(bal[r]);
+        }
+        if (cnt + tot > (uint32_t)kWB) wflush<kOutNode, true>(wb, ws, cnt, o);
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((bal[r] >> lane_id()) & 1u) wb.v[cnt + __popc(bal[r] & lt)] = vv[r];
+            cnt += __popc(bal[r]);
+        }
+        __syncwarp();
+        return;
+    }
     int32_t vb[R], vd[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -538,7 +623,10 @@ __device__ __forceinline__ void set_loop(const StepParams &p, Ctl *ctl, bool mor
     }
     ctl->active = more ? 1u : 0u;
     if (p.use_cond) cudaGraphSetConditional(p.cond, more ? 1u : 0u);
-    if (p.use_cond_small) cudaGraphSetConditional(p.cond_small, (more && ctl->in_edges <= (uint64_t)p.small_edges) ? 1u : 0u);
+    if (p.small_edges > 0) {
+        ctl->small_run = ctl->in_edges <= (uint64_t)p.small_edges ? ctl->small_run + 1u : 0u;
+        if (p.use_cond_small) cudaGraphSetConditional(p.cond_small, (more && ctl->small_run >= kSmallAfter) ? 1u : 0u);
+    }
 }
 
 // Finalise a plain (non-HP) step: the output list becomes the input list.

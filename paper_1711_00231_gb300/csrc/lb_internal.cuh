@@ -29,10 +29,16 @@ constexpr int kBlock = 256;             // threads per CTA of every step kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kTraceMax = 4096;
 constexpr int kHistMax = 4096;  // largest HistogramBinCount
+// The persistent small-list kernel takes over once this many consecutive
+// levels have produced lists of at most small_edges edges: a high-diameter
+// graph has thousands of such levels, a skewed graph only a few at its
+// start and end, where entering the persistent launch costs more than it
+// saves.
+constexpr uint32_t kSmallAfter = 4;
 // Tile starts are recorded every kTileGrain worklist edges; an iteration
 // then cuts its list into tiles of q * kTileGrain edges, q chosen from the
 // list's size so that small lists still spread over many CTAs.
-constexpr int64_t kTileGrain = 256;
+constexpr int64_t kTileGrain = 256;  // a power of two: the flush divides by it with shifts (>> 8)
 
 // error bits in Ctl::error
 enum : uint32_t {
@@ -84,7 +90,7 @@ struct Ctl {
     uint32_t bar_count;     // small-list levels: CTAs arrived at the grid barrier
     uint32_t bar_gen;       // small-list levels: barrier generation
     uint32_t bar_stop;      // small-list levels: the releasing CTA saw the time limit pass
-    uint32_t bar_pad;
+    uint32_t small_run;     // consecutive levels ending with a list of at most small_edges edges
     uint32_t sub_in;    // HP: sub list buffer read when hp_from == kHpFromSub
     uint32_t blocks_done;
     uint32_t active;    // loop condition

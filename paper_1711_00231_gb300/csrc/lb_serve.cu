@@ -486,6 +486,8 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, 
     o.err = &S->error;
     o.pushes = &S->pushes;
     o.child_first = nullptr;
+    o.off = g.off;
+    o.defer = LB_DEFER_OFFSETS;
     uint32_t cnt = 0;
     wd_walk_tile<SSSP, kItems, true>(g, ws_list(st.ws, W, st.par), st.in_cnt, (int64_t)st.in_edges, q * kTileGrain,
                                      t, bitmap, qcur, st.status, st.level, &S->error, wb, ws, cnt, o);

@@ -456,6 +456,8 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     o.mdt = p.mdt;
     o.err = &ctl->error;
     o.pushes = &ctl->pushes;
+    o.off = p.g.off;
+    o.defer = LB_DEFER_OFFSETS;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
     wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, qcur);
@@ -538,7 +540,9 @@ __global__ void __launch_bounds__(kBlock, LB_SMALL_CTAS) k_small_levels(StepPara
     int64_t in_cnt = *(volatile uint32_t *)&ctl->in_cnt;
     int64_t E = (int64_t)*(volatile uint64_t *)&ctl->in_edges;
     // uniform: every CTA reads the same state left by the previous launch
-    if (lim <= 0 || *(volatile uint32_t *)&ctl->active == 0u || in_cnt == 0 || E > lim) return;
+    if (lim <= 0 || *(volatile uint32_t *)&ctl->active == 0u || in_cnt == 0 || E > lim ||
+        *(volatile uint32_t *)&ctl->small_run < kSmallAfter)
+        return;
     uint32_t *status = ctl->status;
     const uint32_t warp = threadIdx.x >> 5;
     const uint64_t step0 = ctl->step;
@@ -571,6 +575,8 @@ __global__ void __launch_bounds__(kBlock, LB_SMALL_CTAS) k_small_levels(StepPara
         o.err = &ctl->error;
         o.pushes = &ctl->pushes;
         o.child_first = nullptr;
+        o.off = p.g.off;
+        o.defer = LB_DEFER_OFFSETS;
         uint32_t cnt = 0;
         const int64_t T = iteration_tile(E, gridDim.x, p.tile);
         const int64_t ntiles = (E + T - 1) / T;

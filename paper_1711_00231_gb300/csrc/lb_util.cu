@@ -69,6 +69,7 @@ __global__ void k_prepare(StepParams p, int32_t src, uint32_t *status, int kind,
     c->small_pack[0] = c->small_pack[1] = c->small_pack[2] = 0ull;
     c->bar_count = 0u;
     c->bar_stop = 0u;
+    c->small_run = 0u;
     c->hp_lvl = 0;
     c->hp_mdt_pending = 0;
     c->sub_maxdeg = 0ull;
