@@ -421,16 +421,26 @@ def serving_bench(args, torch):
         g.sssp_dev(int(cand[gi][0]), "WD", tmp)
     torch.cuda.synchronize()
     one = sv.serve_one_at_a_time(G, burst, outs_a)
-    S = sv.Server(G)
+    # the serving autotuner picks edges per lane, CTAs per SM, tile size and
+    # claiming policy on a sample of the burst (its first 64 requests)
+    t0 = time.time()
+    sample = [(r.graph, r.src, sv.KIND[r.kind]) for r in burst[:64]]
+    tuned, tuned_qps = lb.lb_server_autotune([g.h for g in G], sample)
+    tune = {"options": {k: tuned[k] for k in ("items", "ctas_per_sm", "tile", "policy")}, "sample_qps": tuned_qps,
+            "sample": "first 64 requests of the burst", "seconds": time.time() - t0}
+    S = sv.Server(G, ctas_per_sm=tuned["ctas_per_sm"], tile=tuned["tile"], policy=tuned["policy"],
+                  items=tuned["items"])
     try:
-        return _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffers, one, t_gen)
+        res = _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffers, one, t_gen, tuned)
+        res["autotune"] = tune
+        return res
     finally:
         S.close()
         for g in G:
             g.close()
 
 
-def _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffers, one, t_gen):
+def _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffers, one, t_gen, tuned):
     info = S.info()
     S.run_batch(burst[:64], outs_b[:64])     # warm the persistent kernel
     torch.cuda.synchronize()
@@ -446,8 +456,9 @@ def _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffer
     srv_p = sv.serve(S, pois, outs_b, timeout_s=args.serve_timeout)
     torch.cuda.synchronize()
     exact_p = all(torch.equal(a, b) for a, b in zip(outs_a, outs_b)) and srv_p["statuses_ok"]
-    # the same arrivals with round-robin tile claiming only (policy 1)
-    S_rr = sv.Server(G, policy=1)
+    # the same arrivals with the other claiming policy
+    other = 1 - tuned["policy"]
+    S_rr = sv.Server(G, ctas_per_sm=tuned["ctas_per_sm"], tile=tuned["tile"], policy=other, items=tuned["items"])
     try:
         outs_c = buffers(pois)
         S_rr.run_batch(burst[:64], buffers(burst[:64]))
@@ -474,8 +485,9 @@ def _serving_runs(args, torch, sv, cg, G, S, cand, burst, outs_a, outs_b, buffer
             "poisson_rate_qps": rate,
             "one_at_a_time_latency": {k: one_p[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
             "batched_latency": {k: srv_p[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
-            "batched_latency_round_robin": {k: srv_rr[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
-            "claiming": "oldest query first, then round robin (policy 0); round robin only (policy 1) beside it",
+            f"batched_latency_policy{other}": {k: srv_rr[k] for k in ("p50_ms", "p99_ms", "mean_ms")},
+            "claiming": f"policy {tuned['policy']} (0: oldest query first, then round robin; 1: round robin only); "
+                        f"policy {other} beside it with the other options unchanged",
             "pool_bytes": info["pool_bytes"], "query_bytes_largest_graph": info["slot_bytes"],
             "batched_latency_at_0.8x_batched_capacity": {"rate_qps": rate_hi, **{k: srv_hi[k] for k in
                                                                                  ("p50_ms", "p99_ms", "qps")}},

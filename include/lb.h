@@ -329,7 +329,9 @@ typedef struct lb_server_options {
                              the other queries fill the CTAs it leaves
                              idle), then round robin over the busy slots;
                              1 = round robin only (0) */
-    int32_t reserved[6];
+    int32_t items;        /* edges per thread per round in a RELAX tile: 2
+                             or 3 (0 = 2) */
+    int32_t reserved[5];
 } lb_server_options;
 
 typedef struct lb_server_info_t {
@@ -392,6 +394,19 @@ typedef struct lb_server_state_t {
 } lb_server_state_t;
 
 lb_status lb_server_state(lb_server *s, lb_server_state_t *out);
+
+/* Autotuner of the serving engine: runs the nreq sample requests (graph
+ * index, source, kind; 1..4096 of them) as one batch on a server built with
+ * each candidate of a grid of options -- edges per lane 2 / 3, CTAs per SM
+ * (the occupancy limit / 3), largest tile 4096 / 8192 edges, claiming
+ * policy 0 / 1 -- and returns in *best the candidate with the most
+ * queries/s (second run of each; the first warms up), with that rate in
+ * *best_qps (either may be NULL).  Fields outside the grid come from *base
+ * (NULL: the defaults).  The sample's results go to device buffers the call
+ * allocates and frees; the graphs are only read. */
+lb_status lb_server_autotune(lb_graph *const *graphs, int32_t ngraphs, const lb_server_options *base,
+                             const int32_t *req_graph, const int32_t *req_src, const int32_t *req_kind, int32_t nreq,
+                             lb_server_options *best, double *best_qps);
 
 /* Asks the persistent kernel to leave and waits for it (queries in flight
  * stay in their slots and resume at the next submit / poll). */

@@ -42,15 +42,12 @@ namespace srv {
 
 constexpr uint32_t kRing = 1u << 16;         // request / completion ring entries
 constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
-// edges per thread per round in a RELAX tile, and CTAs per SM the kernel is
-// compiled for (the register budget)
-#ifndef LB_SERVE_ITEMS
-#define LB_SERVE_ITEMS 2
-#endif
+// CTAs per SM the kernel is compiled for (the register budget); the edges
+// per thread per round in a RELAX tile (2 or 3) are a server option, one
+// kernel instance each
 #ifndef LB_SERVE_MIN_BLOCKS
 #define LB_SERVE_MIN_BLOCKS 4
 #endif
-constexpr int kItems = LB_SERVE_ITEMS;
 constexpr int kMaxSlots = 4096;  // slot indices fit 12 bits (Shared::oldest)
 constexpr uint64_t kAdmitPeriodNs = 50000;  // a busy CTA retries admission this often
 
@@ -451,7 +448,7 @@ __device__ void check_tile(const Params &P, Slot *S, int64_t k) {
         if (__ldcg(st.status + i) == kSat) atomicOr(&S->error, kErrOverflow);
 }
 
-template <bool SSSP>
+template <bool SSSP, int ITEMS>
 __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, int64_t q, WarpBuf &wb,
                            WarpScratch &ws) {
     const SlotState st = slot_state(S);
@@ -489,7 +486,7 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, 
     o.off = g.off;
     o.defer = LB_DEFER_OFFSETS;
     uint32_t cnt = 0;
-    wd_walk_tile<SSSP, kItems, true>(g, ws_list(st.ws, W, st.par), st.in_cnt, (int64_t)st.in_edges, q * kTileGrain,
+    wd_walk_tile<SSSP, ITEMS, true>(g, ws_list(st.ws, W, st.par), st.in_cnt, (int64_t)st.in_edges, q * kTileGrain,
                                      t, bitmap, qcur, st.status, st.level, &S->error, wb, ws, cnt, o);
 #if LB_BLOCK_FLUSH
     wflush_block<kOutNode, true>(wb, ws, cnt, o);
@@ -575,6 +572,7 @@ __device__ void release_admit(const Params &P) {
 
 // ---- the persistent kernel -------------------------------------------------
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P) {
     __shared__ WarpBuf s_wb[kWarps];
     __shared__ WarpScratch s_ws[kWarps];
@@ -784,8 +782,8 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
         if (kind == kJobInit) init_tile(P, S, s_tile);
         else if (kind == kJobCheck) check_tile(P, S, s_tile);
         else if (((const volatile Slot *)S)->kind == 1)
-            relax_tile<true>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
-        else relax_tile<false>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
+            relax_tile<true, ITEMS>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
+        else relax_tile<false, ITEMS>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
         // Other CTAs read this tile's stores (list entries, resets) in the
         // slot's next job within this same kernel: they are made visible
         // device-wide before the tile is counted as done.
@@ -1011,7 +1009,8 @@ lb_status launch_kernel(lb_server *s) {
     P.hard_ns = (uint64_t)s->opt.launch_ms * 1000000ull;  // one persistent launch never outlives this
     k_serve_t0<<<1, 1, 0, s->stream>>>(s->d_shared);
     SV_CU(cudaGetLastError(), "k_serve_t0 launch");
-    k_serve<<<s->grid, kBlock, 0, s->stream>>>(P);
+    if (s->opt.items == 3) k_serve<3><<<s->grid, kBlock, 0, s->stream>>>(P);
+    else k_serve<2><<<s->grid, kBlock, 0, s->stream>>>(P);
     SV_CU(cudaGetLastError(), "persistent kernel launch");
     SV_CU(cudaEventRecord(s->ev_kernel, s->stream), "cudaEventRecord");
     s->launched = true;
@@ -1054,9 +1053,10 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
     if (o.idle_us == 0) o.idle_us = 1000;
     if (o.mem_fraction <= 0.0) o.mem_fraction = 0.5;
     if (o.launch_ms == 0) o.launch_ms = 600000;
+    if (o.items == 0) o.items = 2;
     if (o.tile < 256 || o.tile > 8192 || o.tile % 256 || o.slots < 0 || o.slots > kMaxSlots || o.idle_us < 0 ||
         o.mem_fraction > 0.95 || o.ctas_per_sm < 0 || o.ctas_per_sm > 32 || o.launch_ms < 0 || o.policy < 0 ||
-        o.policy > 1) {
+        o.policy > 1 || (o.items != 2 && o.items != 3)) {
         delete s;
         return sfail(LB_ERR_ARG, "bad server options");
     }
@@ -1098,7 +1098,8 @@ lb_status lb_server_create(lb_graph *const *graphs, int32_t ngraphs, const lb_se
         return sfail(LB_ERR_OOM, "not enough free device memory for one query on the largest graph");
     }
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, kBlock, 0);
+    if (o.items == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve<3>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve<2>, kBlock, 0);
     if (occ < 1) occ = 1;
     if (o.ctas_per_sm > 0 && o.ctas_per_sm < occ) occ = o.ctas_per_sm;
     s->grid = occ * s->sms;
@@ -1271,6 +1272,76 @@ lb_status lb_server_state(lb_server *s, lb_server_state_t *out) {
     }
     if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     return st;
+}
+
+lb_status lb_server_autotune(lb_graph *const *graphs, int32_t ngraphs, const lb_server_options *base,
+                             const int32_t *req_graph, const int32_t *req_src, const int32_t *req_kind, int32_t nreq,
+                             lb_server_options *best, double *best_qps) {
+    if (!graphs || ngraphs < 1 || !req_graph || !req_src || !req_kind || nreq < 1 || nreq > 4096)
+        return sfail(LB_ERR_ARG, "need graphs and 1..4096 sample requests");
+    for (int32_t i = 0; i < nreq; ++i) {
+        if (req_graph[i] < 0 || req_graph[i] >= ngraphs || !graphs[req_graph[i]]) return sfail(LB_ERR_ARG, "bad request graph");
+        int64_t n = 0, m = 0;
+        int32_t w = 0, dev = 0;
+        lb_graph_info(graphs[req_graph[i]], &n, &m, &w, &dev);
+        if (req_src[i] < 0 || (int64_t)req_src[i] >= n) return sfail(LB_ERR_ARG, "bad request source");
+        if (req_kind[i] != LB_KIND_BFS && (req_kind[i] != LB_KIND_SSSP || !w)) return sfail(LB_ERR_ARG, "bad request kind");
+    }
+    lb_server_options o0;
+    memset(&o0, 0, sizeof(o0));
+    if (base) o0 = *base;
+    // one output buffer per sample request, sized for its graph
+    std::vector<void *> outs((size_t)nreq, nullptr);
+    lb_status st = LB_OK;
+    for (int32_t i = 0; i < nreq && st == LB_OK; ++i) {
+        int64_t n = 0;
+        lb_graph_info(graphs[req_graph[i]], &n, nullptr, nullptr, nullptr);
+        if (cudaMalloc(&outs[(size_t)i], 4 * (size_t)n) != cudaSuccess) st = sfail(LB_ERR_OOM, "sample output buffers");
+    }
+    double top = -1.0;
+    lb_server_options top_o = o0;
+    std::vector<lb_completion> done(256);
+    // candidate grid: edges per lane, CTAs per SM, largest tile, claiming policy
+    for (int32_t items : {2, 3})
+        for (int32_t ctas : {0, 3})
+            for (int32_t tile : {4096, 8192})
+                for (int32_t policy : {0, 1}) {
+                    if (st != LB_OK) break;
+                    lb_server_options o = o0;
+                    o.items = items;
+                    o.ctas_per_sm = ctas;
+                    o.tile = tile;
+                    o.policy = policy;
+                    lb_server *s = nullptr;
+                    st = lb_server_create(graphs, ngraphs, &o, &s);
+                    if (st != LB_OK) break;
+                    double dt = 0.0;
+                    for (int rep = 0; rep < 2 && st == LB_OK; ++rep) {  // the first run warms up
+                        const auto t0 = std::chrono::steady_clock::now();
+                        for (int32_t i = 0; i < nreq && st == LB_OK; ++i)
+                            st = lb_server_submit(s, req_graph[i], req_src[i], req_kind[i], outs[(size_t)i], nullptr);
+                        int32_t left = nreq;
+                        while (left > 0 && st == LB_OK) {
+                            int32_t nd = 0;
+                            st = lb_server_poll(s, done.data(), (int32_t)done.size(), &nd);
+                            left -= nd;
+                            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(300))
+                                st = sfail(LB_ERR_TIMEOUT, "a sample batch ran past 300 s");
+                        }
+                        dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                    }
+                    lb_server_destroy(s);
+                    if (st == LB_OK && nreq / dt > top) {
+                        top = nreq / dt;
+                        top_o = o;
+                    }
+                }
+    for (void *p : outs)
+        if (p) cudaFree(p);
+    if (st != LB_OK) return st;
+    if (best) *best = top_o;
+    if (best_qps) *best_qps = top;
+    return LB_OK;
 }
 
 lb_status lb_server_stop(lb_server *s) {

@@ -282,7 +282,6 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
     const int64_t ntiles = (E + T - 1) / T;
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t upto = (2u << lane) - 1u;  // bits 0..lane
     const int64_t e0 = t * T;
     const int64_t e1 = min(e0 + T, E);
     const int64_t i0 = ld_list<COH>(in.tstart + t * q);
@@ -366,11 +365,12 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
                     u0 = u1;
                     load(kb + 32 + (int32_t)lane, s1, d1, u1);
                 }
-                const int32_t p0 = s0 - ew, p1 = s1 - ew;  // entries starting after ew have p > 0
-                const uint32_t bits =
-                    ((p0 > 0 && p0 < 32) ? (1u << p0) : 0u) | ((p1 > 0 && p1 < 32) ? (1u << p1) : 0u);
+                // bit p - 1 of `starts`: an entry starts at ew + p, for p = 1..32
+                // (entries have at least one edge, so at most 32 start there)
+                const int32_t p0 = s0 - ew - 1, p1 = s1 - ew - 1;
+                const uint32_t bits = ((uint32_t)p0 < 32u ? (1u << p0) : 0u) | ((uint32_t)p1 < 32u ? (1u << p1) : 0u);
                 const uint32_t starts = __reduce_or_sync(kFull, bits);
-                const int32_t pe = kcur - kb + __popc(starts & upto);  // window position of my entry
+                const int32_t pe = kcur - kb + __popc(starts & lanemask_lt());  // window position of my entry
                 const int32_t x0 = __shfl_sync(kFull, d0, pe & 31);
                 const int32_t x1 = __shfl_sync(kFull, d1, pe & 31);
                 uint32_t du = 0u;
@@ -394,7 +394,7 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
                     }
                 }
                 // the entry holding the next step's first edge
-                kcur += __popc(starts) + (__ballot_sync(kFull, p0 == 32 || p1 == 32) != 0u ? 1 : 0);
+                kcur += __popc(starts);
                 ew += 32;
             }
         }

@@ -94,7 +94,25 @@ __global__ void k_init(StepParams p) {
     const int64_t n = p.g.n;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n; i += stride) status[i] = i == src ? 0u : kInf;
+    if (((uintptr_t)status & 15u) == 0) {
+        // 16-byte stores (the output buffer is usually 16-byte aligned)
+        uint4 *s4 = reinterpret_cast<uint4 *>(status);
+        const int64_t n4 = n / 4;
+        for (int64_t i = tid; i < n4; i += stride) {
+            uint4 x = make_uint4(kInf, kInf, kInf, kInf);
+            if (i == src / 4) {
+                const int32_t k = src % 4;
+                if (k == 0) x.x = 0u;
+                else if (k == 1) x.y = 0u;
+                else if (k == 2) x.z = 0u;
+                else x.w = 0u;
+            }
+            s4[i] = x;
+        }
+        for (int64_t i = 4 * n4 + tid; i < n; i += stride) status[i] = i == src ? 0u : kInf;
+    } else {
+        for (int64_t i = tid; i < n; i += stride) status[i] = i == src ? 0u : kInf;
+    }
     if (!sssp) {
         // BFS: the visited bits (first half), the source already visited
         const int64_t words = (n + 31) / 32;

@@ -64,7 +64,7 @@ class lb_query_stats(ctypes.Structure):
 class lb_server_options(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("idle_us", ctypes.c_int32), ("mem_fraction", ctypes.c_double), ("launch_ms", ctypes.c_int32),
-                ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("policy", ctypes.c_int32), ("items", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class lb_server_info_t(ctypes.Structure):
@@ -141,6 +141,8 @@ def _load():
         "lb_server_submit": ([P, i32, i32, i32, P, ctypes.POINTER(ctypes.c_uint64)], st),
         "lb_server_poll": ([P, P, i32, ctypes.POINTER(i32)], st),
         "lb_server_stop": ([P], st),
+        "lb_server_autotune": ([P, i32, ctypes.POINTER(lb_server_options), P, P, P, i32,
+                                ctypes.POINTER(lb_server_options), ctypes.POINTER(ctypes.c_double)], st),
         "lb_server_state": ([P, ctypes.POINTER(lb_server_state_t)], st),
         "lb_last_error": ([], ctypes.c_char_p),
         "lb_version": ([], ctypes.c_char_p),
@@ -343,12 +345,28 @@ def lb_bfs_wd_noalloc(offsets_dev, cols_dev, n: int, m: int, src: int, levels_de
                                      _stream_handle(stream)))
 
 
+def lb_server_autotune(graphs, requests, **base) -> tuple:
+    """Best server options for a sample of requests [(graph, src, kind)]:
+    returns (options dict, queries/s)."""
+    arr = (ctypes.c_void_p * len(graphs))(*graphs)
+    g = np.ascontiguousarray([r[0] for r in requests], dtype=np.int32)
+    sr = np.ascontiguousarray([r[1] for r in requests], dtype=np.int32)
+    k = np.ascontiguousarray([r[2] for r in requests], dtype=np.int32)
+    b = lb_server_options(**base)
+    o = lb_server_options()
+    q = ctypes.c_double()
+    _check(_load().lb_server_autotune(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(b), _ptr(g), _ptr(sr),
+                                      _ptr(k), len(requests), ctypes.byref(o), ctypes.byref(q)))
+    return {f: (float(getattr(o, f)) if f == "mem_fraction" else int(getattr(o, f)))
+            for f, _ in o._fields_ if f != "reserved"}, float(q.value)
+
+
 def lb_server_create(graphs, slots: int = 0, ctas_per_sm: int = 0, tile: int = 0, idle_us: int = 0,
-                     mem_fraction: float = 0.0, launch_ms: int = 0, policy: int = 0) -> int:
+                     mem_fraction: float = 0.0, launch_ms: int = 0, policy: int = 0, items: int = 0) -> int:
     """Persistent multi-query engine over resident graphs (lb_graph handles)."""
     arr = (ctypes.c_void_p * len(graphs))(*graphs)
     o = lb_server_options(slots=slots, ctas_per_sm=ctas_per_sm, tile=tile, idle_us=idle_us, mem_fraction=mem_fraction,
-                          launch_ms=launch_ms, policy=policy)
+                          launch_ms=launch_ms, policy=policy, items=items)
     h = ctypes.c_void_p()
     _check(_load().lb_server_create(ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(o), ctypes.byref(h)))
     return h.value

@@ -33,10 +33,10 @@ class Request:
 
 class Server:
     def __init__(self, graphs: Sequence["lb.Graph"], slots: int = 0, ctas_per_sm: int = 0, tile: int = 0,
-                 idle_us: int = 0, mem_fraction: float = 0.0, launch_ms: int = 0, policy: int = 0):
+                 idle_us: int = 0, mem_fraction: float = 0.0, launch_ms: int = 0, policy: int = 0, items: int = 0):
         self.graphs = list(graphs)
         self.h = lb.lb_server_create([g.h for g in self.graphs], slots, ctas_per_sm, tile, idle_us, mem_fraction,
-                                     launch_ms, policy)
+                                     launch_ms, policy, items)
 
     def submit(self, graph: int, src: int, kind: str, out_dev) -> int:
         if 0 <= graph < len(self.graphs):

@@ -256,3 +256,29 @@ def test_admission_by_memory_queues_what_does_not_fit():
     finally:
         for h in handles:
             h.close()
+
+
+def test_server_autotune_picks_grid_options(mix):
+    # the serving autotuner runs a sample batch under each candidate of its
+    # grid and returns the fastest; a server built with it gives exact results
+    import torch
+    graphs, handles = mix
+    reqs = make_requests(graphs, 24, seed=21)
+    sample = [(r.graph, r.src, sv.KIND[r.kind]) for r in reqs]
+    best, qps = lb.lb_server_autotune([h.h for h in handles], sample, slots=16)
+    assert qps > 0
+    assert best["items"] in (2, 3) and best["ctas_per_sm"] in (0, 3) and best["tile"] in (4096, 8192)
+    assert best["policy"] in (0, 1) and best["slots"] == 16
+    S = sv.Server(handles, slots=best["slots"], ctas_per_sm=best["ctas_per_sm"], tile=best["tile"],
+                  policy=best["policy"], items=best["items"])
+    try:
+        outs = [torch.full((graphs[r.graph].n,), 7, dtype=torch.int32, device="cuda") for r in reqs]
+        assert all(x == 0 for x in S.run_batch(reqs, outs, timeout_s=120))
+        torch.cuda.synchronize()
+        for r, o in zip(reqs, outs):
+            assert np.array_equal(o.cpu().numpy(), reference(graphs[r.graph], r.kind, r.src)), r
+    finally:
+        S.close()
+    with pytest.raises(lb.LbError) as ei:
+        lb.lb_server_autotune([h.h for h in handles], [(0, graphs[0].n, 0)])
+    assert ei.value.status == lb.LB_ERR_ARG
