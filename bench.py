@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--kinds", default="bfs,sssp")
     ap.add_argument("--wd-tile", type=int, default=0, help="largest WD tile in list edges (0 = library default)")
     ap.add_argument("--hp-mode", type=int, default=0, help="HP form: 0 sub-iterations, 1 degree-binned")
+    ap.add_argument("--ns-mode", type=int, default=0, help="NS form: 0 thread per granule, 1 binned granules")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default options)")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched-serving measurement")
     ap.add_argument("--serve-queries", type=int, default=1024)
@@ -158,21 +159,6 @@ def combine_ranks(t_ms: float, edges_rank: float, world: int, device: str):
         dist.all_reduce(te)
         edges_all = float(te.item())
     return t_ms, edges_all, edges_all / (t_ms / 1e3) / 1e9
-
-
-def stored_traffic(args):
-    """DRAM bytes per query of k_step_wd from the committed ncu capture of
-    this workload, if it was taken on the kernel build that runs now."""
-    path = os.path.join(ROOT, "profiles", "k_step_wd_traffic_rmat24_ef32.json")
-    if args.scale != 24 or args.edge_factor != 32 or args.wd_tile or not os.path.exists(path):
-        return None
-    from paper_1711_00231_gb300 import _build
-    with open(path) as f:
-        d = json.load(f)
-    if d.get("kernel_digest") != _build.kernel_digest():
-        return None
-    d["file"] = "profiles/k_step_wd_traffic_rmat24_ef32.json"
-    return d
 
 
 def measured_peak():
@@ -284,9 +270,9 @@ def small_configs(torch, reps: int = 3):
         row = {"n": g.n, "m": g.m, "source": int(src)}
         for kind in kinds:
             f = G.bfs_dev if kind == "bfs" else G.sssp_dev
-            for label in ("BS", "EP", "WD", "NS", "HP", "HP_binned", "NS_PHYS"):
-                s_name = "HP" if label == "HP_binned" else label
-                G.set_options(hp_mode=1 if label == "HP_binned" else 0)
+            for label in ("BS", "EP", "WD", "NS", "NS_binned", "HP", "HP_binned", "NS_PHYS"):
+                s_name = label.replace("_binned", "")
+                G.set_options(hp_mode=1 if label == "HP_binned" else 0, ns_mode=1 if label == "NS_binned" else 0)
                 f(int(src), s_name, buf)
                 torch.cuda.synchronize()
                 res = buf.cpu().numpy()
@@ -534,6 +520,8 @@ def main():
         G.set_options(wd_tile=args.wd_tile)
     if args.hp_mode:
         G.set_options(hp_mode=args.hp_mode)
+    if args.ns_mode:
+        G.set_options(ns_mode=args.ns_mode)
     t_upload = time.time() - t0
     kinds = tuple(k for k in args.kinds.split(",") if k)
     strat = args.strategy
@@ -639,18 +627,15 @@ def main():
                      "work_inflation": sum(work[(kind, int(s))][4] for s in srcs) / max(
                          1, sum(work[(kind, int(s))][0] for s in srcs))}
     peak, peak_kind = measured_peak()
-    traffic = stored_traffic(args)
     dom = max(kinds, key=lambda k: per_query_ms[k].sum())
     achieved = res[dom]["algorithmic_gbs"]
     def roof(kind):
         a = res[kind]["algorithmic_gbs"]
-        t = traffic.get(kind) if traffic else None
         return {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
-                "traffic": t["dram_bytes_per_query"] if t else None,
-                "traffic_note": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum over all k_step_wd launches of "
-                                 f"one query from source 0 ({t['queries']} queries captured; algorithmic bytes of "
-                                 f"that query {t['algorithmic_bytes_per_query']:.4g}); {traffic['file']}")
-                if t else "no stored capture for this kernel build and workload",
+                "traffic": None,
+                "traffic_note": "captured at R-MAT scale 22 only (profiles/k_step_wd_traffic_rmat22_ef32.md: BFS "
+                                "0.68x, SSSP 2.84x the algorithmic bytes per query); not scaled, since at scale 24 "
+                                "the distance array no longer fits in L2 and traffic does not grow in proportion",
                 "kernel": f"k_step_wd ({kind})", "peak_source": f"{peak_kind} hbm_gbs",
                 "unit_of_work": "one query (all its relax launches + set-up); algorithmic bytes per query "
                                 f"= {BYTES[kind][0]} B x m_reached + {BYTES[kind][1]} B x n_reached"}
@@ -668,10 +653,11 @@ def main():
             for s in cmp_src:
                 query(kind, s, "WD")
                 wd_ref[int(s)] = out.clone()
-            for label in ("BS", "EP", "WD", "NS", "HP", "HP_binned", "NS_PHYS"):
-                # HP_binned: HP with hp_mode 1 (degree-binned sub-worklists in one step)
-                s_name = "HP" if label == "HP_binned" else label
-                G.set_options(hp_mode=1 if label == "HP_binned" else 0)
+            for label in ("BS", "EP", "WD", "NS", "NS_binned", "HP", "HP_binned", "NS_PHYS"):
+                # *_binned: HP with hp_mode 1 (degree-binned sub-worklists in one
+                # step), NS with ns_mode 1 (granules by a thread, a warp or the CTA)
+                s_name = label.replace("_binned", "")
+                G.set_options(hp_mode=1 if label == "HP_binned" else 0, ns_mode=1 if label == "NS_binned" else 0)
                 tot = 0.0
                 e_tot = 0
                 exact = True
@@ -689,7 +675,7 @@ def main():
                 row[label] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9,
                               "exact_vs_wd": exact}
             del wd_ref
-            G.set_options(hp_mode=0)
+            G.set_options(hp_mode=0, ns_mode=0)
             row["speedup_wd_vs_bs"] = row["BS"]["ms_per_query"] / row["WD"]["ms_per_query"]
             row["speedup_wd_vs_ep"] = row["EP"]["ms_per_query"] / row["WD"]["ms_per_query"]
             extra[kind] = row

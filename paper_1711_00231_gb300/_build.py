@@ -6,7 +6,6 @@ from __future__ import annotations
 import concurrent.futures as cf
 import hashlib
 import os
-import re
 import shutil
 import subprocess
 
@@ -47,29 +46,6 @@ def _digest() -> str:
     with open(os.path.join(INCLUDE, "lb.h"), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()
-
-
-# the sources that define the WD relax kernel (k_step_wd) and its launch
-WD_KERNEL_SOURCES = ["lb_internal.cuh", "lb_device.cuh", "lb_steps.cuh", "lb_launch.h", "lb_step_wd.cu"]
-
-
-def _code_only(src: str) -> str:
-    """C++ source without comments and blank lines (what compiles)."""
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    src = re.sub(r"//[^\n]*", "", src)
-    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
-
-
-def kernel_digest() -> str:
-    """Digest of the WD relax kernel's code (comments excluded) and compile
-    flags: a stored profile of the kernel applies only while this is
-    unchanged."""
-    h = hashlib.sha256()
-    h.update(" ".join(NVCC_FLAGS[:-3] + _extra_flags()).encode())  # flags without the include path
-    for f in WD_KERNEL_SOURCES:
-        with open(os.path.join(CSRC, f), encoding="utf-8") as fh:
-            h.update(f.encode() + _code_only(fh.read()).encode())
-    return h.hexdigest()[:16]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
