@@ -37,16 +37,27 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // what a flush writes
 enum : int { kOutNode = 0, kOutGranule = 1, kOutEdges = 2, kOutEdgesPerEdge = 3, kOutPhys = 4 };
 
-struct WarpBuf {
-    int32_t beg[kWB];
-    int32_t v[kWB];
-    uint32_t deg[kWB];
+// A warp's push buffer of N entries in shared memory.  The shared-memory
+// footprint sets the L1 / shared-memory carve-out: a smaller buffer leaves
+// more L1 for the randomly read visited bitmap (BFS).
+template <int N>
+struct WarpBufT {
+    static constexpr int kCap = N;
+    int32_t beg[N];
+    int32_t v[N];
+    uint32_t deg[N];
 };
+using WarpBuf = WarpBufT<kWB>;
 
-struct WarpScratch {
-    uint32_t pu[kWB];  // exclusive prefix of output units
-    uint32_t pe[kWB];  // exclusive prefix of edges
+// Prefix scratch of a flush that expands entries into granules or edges (a
+// binary search over the output units); node flushes need none.
+template <int N>
+struct WarpScratchT {
+    uint32_t pu[N];  // exclusive prefix of output units
+    uint32_t pe[N];  // exclusive prefix of edges
 };
+using WarpScratch = WarpScratchT<kWB>;
+struct NoScratch {};
 
 struct FlushOut {
     NodeList list;     // node / granule output
@@ -65,6 +76,18 @@ struct FlushOut {
     // relax group) and drops vertices without out-edges
     const int64_t *off = nullptr;
     int32_t defer = 0;
+    // defer == 3 (SSSP): the buffer holds (vertex, offered distance) pairs
+    // whose plain check passed; the flush makes their atomicMin and, for
+    // the improved vertices, the queued-bit claim.
+    // defer == 2 (BFS): the buffer holds visited-check candidates, not yet
+    // claimed; the flush claims them all at once (one atomicOr per entry,
+    // every claim of the warp in flight together), writes the new level of
+    // the vertices it won and drops the rest with the vertices that have no
+    // out-edges.  The claim then leaves each relax group's chain of
+    // dependent accesses.
+    uint32_t *claim_bitmap = nullptr;
+    uint32_t *claim_status = nullptr;
+    uint32_t claim_level = 0;
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -84,13 +107,14 @@ __device__ __forceinline__ uint32_t out_units(uint32_t deg, int32_t mdt) {
 }
 
 // Warp-uniform: every lane of the warp calls it with the same cnt.
-// Requires cnt + 32 <= kWB on entry.  The warp synchronises its buffer
+// Requires cnt + 32 <= capacity on entry.  The warp synchronises its buffer
 // writes here (LB_PUSH_SYNC = 1) or once at the start of the flush that
 // reads them (0).
 #ifndef LB_PUSH_SYNC
 #define LB_PUSH_SYNC 1
 #endif
-__device__ __forceinline__ void wpush(WarpBuf &b, uint32_t &cnt, bool want, int32_t v, int64_t beg, uint32_t deg) {
+template <class WB>
+__device__ __forceinline__ void wpush(WB &b, uint32_t &cnt, bool want, int32_t v, int64_t beg, uint32_t deg) {
     // beg < m < 2^31: stored in 32 bits
     const unsigned m = __ballot_sync(kFull, want);
     if (want) {
@@ -124,17 +148,108 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *a, uint32_t n, ui
 #else
 #define LB_FLUSH_INLINE inline
 #endif
-// The two halves of a flush: the warp's exclusive prefix of output units and
-// edges over its buffered entries (into `s`), and the writes at the list
+
+// Output units of buffered entry i (a node list entry; with deferred
+// offsets 0 for a node without out-edges, which is dropped).
+template <int KIND, class WB>
+__device__ __forceinline__ uint32_t entry_units(const WB &b, uint32_t i, uint32_t cnt, const FlushOut &o,
+                                                uint32_t &d) {
+    d = i < cnt ? b.deg[i] : 0u;
+    return (i < cnt && !(KIND == kOutNode && o.defer && d == 0u)) ? out_units<KIND>(d, o.mdt) : 0u;
+}
+
+// Inclusive warp scan of (u, e) pairs.
+__device__ __forceinline__ void warp_scan2(uint32_t &iu, uint32_t &ie, uint32_t lane) {
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const uint32_t tu = __shfl_up_sync(kFull, iu, k);
+        const uint32_t te = __shfl_up_sync(kFull, ie, k);
+        if ((int)lane >= k) { iu += tu; ie += te; }
+    }
+}
+
+// The two halves of a flush.  The first completes the buffered entries
+// (deferred claims and offsets) and totals their output units and edges;
+// for granule / edge outputs it also stores each entry's exclusive prefix
+// in `s` for the expansion.  The second writes the entries at the list
 // position / edge prefix `old` (packed entries << 32 | edges) reserved for
-// them.
-template <int KIND>
-__device__ __forceinline__ void wflush_prefix(WarpBuf &b, WarpScratch &s, uint32_t cnt, const FlushOut &o,
-                                              uint32_t &run_u, uint32_t &run_e) {
+// them; a node flush recomputes its prefix there with a warp scan per 32
+// entries, so it needs no scratch.
+template <int KIND, class WB, class WS>
+__device__ __forceinline__ void wflush_prefix(WB &b, WS &s, uint32_t cnt, const FlushOut &o, uint32_t &run_u,
+                                              uint32_t &run_e) {
     const uint32_t lane = lane_id();
     run_u = 0;
     run_e = 0;
-    if (KIND == kOutNode && o.defer) {
+    if (KIND == kOutNode && o.defer == 2) {
+        constexpr int kPer = WB::kCap / 32;
+        int32_t cv[kPer];
+        uint32_t pv[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t i = lane + 32u * k;
+            cv[k] = i < cnt ? b.v[i] : -1;
+            pv[k] = 0xFFFFFFFFu;
+            if (cv[k] >= 0) pv[k] = atomicOr(o.claim_bitmap + ((uint32_t)cv[k] >> 5), 1u << ((uint32_t)cv[k] & 31u));
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t i = lane + 32u * k;
+            const bool won = cv[k] >= 0 && !((pv[k] >> ((uint32_t)cv[k] & 31u)) & 1u);
+            int32_t b0 = 0, d = 0;
+            if (won) {
+                o.claim_status[cv[k]] = o.claim_level + 1u;
+                // offsets are < m < 2^31 (checked when the graph is created)
+                b0 = (int32_t)__ldg(o.off + cv[k]);
+                d = (int32_t)__ldg(o.off + cv[k] + 1) - b0;
+            }
+            if (i < cnt) {
+                b.beg[i] = b0;
+                b.deg[i] = (uint32_t)d;
+            }
+        }
+        __syncwarp();
+    } else if (KIND == kOutNode && o.defer == 3) {
+        // SSSP: entry i holds a candidate vertex and the distance it was
+        // offered (in beg); the atomicMin of every entry, then the queued
+        // bit of every improved vertex, all in flight together
+        constexpr int kPer = WB::kCap / 32;
+        int32_t cv[kPer];
+        uint32_t pv[kPer], val[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t i = lane + 32u * k;
+            cv[k] = i < cnt ? b.v[i] : -1;
+            val[k] = i < cnt ? (uint32_t)b.beg[i] : 0u;
+            pv[k] = 0u;
+            if (cv[k] >= 0) pv[k] = atomicMin(o.claim_status + cv[k], val[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const bool improved = cv[k] >= 0 && val[k] < pv[k];
+            if (improved && val[k] == kSat) atomicOr(o.err, kErrSaturated);
+            pv[k] = 0xFFFFFFFFu;
+            if (improved)
+                pv[k] = atomicOr(o.claim_bitmap + ((uint32_t)cv[k] >> 5), 1u << ((uint32_t)cv[k] & 31u));
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t i = lane + 32u * k;
+            // queued by the first improvement of this iteration only
+            const bool first = cv[k] >= 0 && !((pv[k] >> ((uint32_t)cv[k] & 31u)) & 1u);
+            int32_t b0 = 0, d = 0;
+            if (first) {
+                // offsets are < m < 2^31 (checked when the graph is created)
+                b0 = (int32_t)__ldg(o.off + cv[k]);
+                d = (int32_t)__ldg(o.off + cv[k] + 1) - b0;
+            }
+            if (i < cnt) {
+                b.beg[i] = b0;
+                b.deg[i] = (uint32_t)d;
+            }
+        }
+        __syncwarp();
+    } else if (KIND == kOutNode && o.defer) {
         // offsets are < m < 2^31 (checked when the graph is created)
         for (uint32_t i = lane; i < cnt; i += 32) {
             const int32_t v = b.v[i];
@@ -144,26 +259,31 @@ __device__ __forceinline__ void wflush_prefix(WarpBuf &b, WarpScratch &s, uint32
         }
         __syncwarp();
     }
-    for (uint32_t c = 0; c < cnt; c += 32) {
-        const uint32_t i = c + lane;
-        const uint32_t d = i < cnt ? b.deg[i] : 0u;
-        // with deferred offsets a buffered node without out-edges is dropped
-        const uint32_t u = (i < cnt && !(KIND == kOutNode && o.defer && d == 0u)) ? out_units<KIND>(d, o.mdt) : 0u;
-        uint32_t iu = u, ie = d;
-#pragma unroll
-        for (int k = 1; k < 32; k <<= 1) {
-            const uint32_t tu = __shfl_up_sync(kFull, iu, k);
-            const uint32_t te = __shfl_up_sync(kFull, ie, k);
-            if ((int)lane >= k) { iu += tu; ie += te; }
+    if constexpr (KIND == kOutNode) {
+        uint32_t su = 0, se = 0;
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            uint32_t d;
+            su += entry_units<KIND>(b, i, cnt, o, d);
+            se += d;
         }
-        if (i < cnt) { s.pu[i] = run_u + iu - u; s.pe[i] = run_e + ie - d; }
-        run_u += __shfl_sync(kFull, iu, 31);
-        run_e += __shfl_sync(kFull, ie, 31);
+        run_u = __reduce_add_sync(kFull, su);
+        run_e = __reduce_add_sync(kFull, se);
+    } else {
+        for (uint32_t c = 0; c < cnt; c += 32) {
+            const uint32_t i = c + lane;
+            uint32_t d;
+            const uint32_t u = entry_units<KIND>(b, i, cnt, o, d);
+            uint32_t iu = u, ie = d;
+            warp_scan2(iu, ie, lane);
+            if (i < cnt) { s.pu[i] = run_u + iu - u; s.pe[i] = run_e + ie - d; }
+            run_u += __shfl_sync(kFull, iu, 31);
+            run_e += __shfl_sync(kFull, ie, 31);
+        }
     }
 }
 
-template <int KIND, bool TILED>
-__device__ __forceinline__ void wflush_write(const WarpBuf &b, const WarpScratch &s, uint32_t &cnt, const FlushOut &o,
+template <int KIND, bool TILED, class WB, class WS>
+__device__ __forceinline__ void wflush_write(const WB &b, const WS &s, uint32_t &cnt, const FlushOut &o,
                                              unsigned long long old, uint32_t run_u) {
     const uint32_t lane = lane_id();
     const int64_t ubase = (int64_t)(old >> 32);
@@ -174,24 +294,33 @@ __device__ __forceinline__ void wflush_write(const WarpBuf &b, const WarpScratch
         __syncwarp();
         return;
     }
-    if (KIND == kOutNode) {
-        for (uint32_t i = lane; i < cnt; i += 32) {
-            if (o.defer && b.deg[i] == 0u) continue;  // deferred offsets: a node without out-edges
-            const int64_t pos = ubase + s.pu[i];
-            const int64_t S = ebase + s.pe[i];
-            o.list.v[pos] = b.v[i];
-            o.list.beg[pos] = b.beg[i];
-            o.list.scan[pos] = (int32_t)S;
-            if (TILED) {
-                const int64_t E = S + b.deg[i];
-                if (o.tile == (int32_t)kTileGrain) {  // the hot path: shifts, no division
-                    for (int64_t k = (S + kTileGrain - 1) >> 8; (k << 8) < E; ++k)
-                        if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
-                } else {
-                    for (int64_t k = (S + o.tile - 1) / o.tile; k * o.tile < E; ++k)
-                        if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+    if constexpr (KIND == kOutNode) {
+        uint32_t ru = 0, re = 0;
+        for (uint32_t c = 0; c < cnt; c += 32) {
+            const uint32_t i = c + lane;
+            uint32_t d;
+            const uint32_t u = entry_units<KIND>(b, i, cnt, o, d);
+            uint32_t iu = u, ie = d;
+            warp_scan2(iu, ie, lane);
+            if (u) {  // a node list entry (deferred offsets: one with out-edges)
+                const int64_t pos = ubase + ru + iu - u;
+                const int64_t S = ebase + re + ie - d;
+                o.list.v[pos] = b.v[i];
+                o.list.beg[pos] = b.beg[i];
+                o.list.scan[pos] = (int32_t)S;
+                if (TILED) {
+                    const int64_t E = S + d;
+                    if (o.tile == (int32_t)kTileGrain) {  // the hot path: shifts, no division
+                        for (int64_t k = (S + kTileGrain - 1) >> 8; (k << 8) < E; ++k)
+                            if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+                    } else {
+                        for (int64_t k = (S + o.tile - 1) / o.tile; k * o.tile < E; ++k)
+                            if (k < o.tile_cap) o.list.tstart[k] = (int32_t)pos;
+                    }
                 }
             }
+            ru += __shfl_sync(kFull, iu, 31);
+            re += __shfl_sync(kFull, ie, 31);
         }
     } else {
         for (uint32_t j = lane; j < run_u; j += 32) {
@@ -212,8 +341,8 @@ __device__ __forceinline__ void wflush_write(const WarpBuf &b, const WarpScratch
     __syncwarp();
 }
 
-template <int KIND, bool TILED>
-__device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
+template <int KIND, bool TILED, class WB, class WS>
+__device__ LB_FLUSH_INLINE void wflush(WB &b, WS &s, uint32_t &cnt, const FlushOut &o) {
     if (cnt == 0) return;
     if (!LB_PUSH_SYNC) __syncwarp();
     const uint32_t lane = lane_id();
@@ -235,8 +364,8 @@ __device__ LB_FLUSH_INLINE void wflush(WarpBuf &b, WarpScratch &s, uint32_t &cnt
 // many small pushes (a grid's SSSP wavefront) thousands of same-address
 // atomics per iteration would queue at one L2 slice.  The packed add is
 // exact: a list's entries and its edges (< m < 2^31) each fit their half.
-template <int KIND, bool TILED>
-__device__ void wflush_block(WarpBuf &b, WarpScratch &s, uint32_t &cnt, const FlushOut &o) {
+template <int KIND, bool TILED, class WB, class WS>
+__device__ void wflush_block(WB &b, WS &s, uint32_t &cnt, const FlushOut &o) {
     __shared__ unsigned long long s_tot[kWarps];
     __shared__ unsigned long long s_base;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -351,15 +480,15 @@ __device__ __forceinline__ uint32_t ld_mut(const uint32_t *p) {
 #ifndef LB_EARLY_EXIT
 #define LB_EARLY_EXIT 1
 #endif
-// FLUSH = false: the caller flushes; then cnt + 32 * ITEMS <= kWB on entry.
+// FLUSH = false: the caller flushes; then cnt + 32 * ITEMS <= capacity on entry.
 // With FlushOut::defer set (kOutNode) only the vertex is buffered.
-template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false, bool FLUSH = true>
+template <bool SSSP, int ITEMS, int KIND, bool TILED, bool COH = false, bool FLUSH = true, class WB, class WS>
 __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32_t (&vv)[ITEMS],
                                             const uint32_t (&ww)[ITEMS], const uint32_t (&dd)[ITEMS],
                                             const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
                                             uint32_t *__restrict__ qcur, uint32_t *__restrict__ status,
-                                            uint32_t level, uint32_t *err, WarpBuf &wb,
-                                            WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+                                            uint32_t level, uint32_t *err, WB &wb,
+                                            WS &ws, uint32_t &cnt, const FlushOut &o) {
     bool cand[ITEMS];
     uint32_t val[ITEMS];
 #pragma unroll
@@ -426,7 +555,7 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it) {
             wpush(wb, cnt, won[it], vv[it], 0, 0u);
-            if (FLUSH && cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
+            if (FLUSH && cnt > WB::kCap - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
         }
         return;
     }
@@ -459,7 +588,7 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
     for (int it = 0; it < ITEMS; ++it) {
         const bool want = won[it] && ve[it] > vb[it];
         wpush(wb, cnt, want, vv[it], vb[it], (uint32_t)(ve[it] - vb[it]));
-        if (FLUSH && cnt > kWB - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
+        if (FLUSH && cnt > WB::kCap - 32) wflush<KIND, TILED>(wb, ws, cnt, o);
     }
 }
 
@@ -478,13 +607,13 @@ __device__ __forceinline__ void relax_items(const bool (&ok)[ITEMS], const int32
 // an unvisited vertex) the claims, then (only if some lane won one) the
 // level writes, offset loads and one push of all won vertices with edges.
 // The push buffer is flushed only when this group's pushes would not fit,
-// so flushes carry close to kWB entries.  Requires R * 32 <= kWB.
-template <int R, bool COH>
+// so flushes carry close to a full buffer.  Requires R * 32 <= capacity.
+template <int R, bool COH, class WB, class WS>
 __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_t (&vv)[R],
                                                const int64_t *__restrict__ off, uint32_t *__restrict__ bitmap,
-                                               uint32_t *__restrict__ status, uint32_t level, WarpBuf &wb,
-                                               WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
-    static_assert(R * 32 <= kWB, "push buffer too small for one group");
+                                               uint32_t *__restrict__ status, uint32_t level, WB &wb,
+                                               WS &ws, uint32_t &cnt, const FlushOut &o) {
+    static_assert(R * 32 <= WB::kCap, "push buffer too small for one group");
     uint32_t cand = 0;  // bit r: item r found v unvisited
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -492,6 +621,25 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
         if (!((x >> ((uint32_t)vv[r] & 31u)) & 1u)) cand |= 1u << r;
     }
     if (!__any_sync(kFull, cand != 0u)) return;
+    if (o.defer == 2) {
+        // deferred claims: buffer the candidates; the flush claims them
+        unsigned bal[R];
+        uint32_t tot = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            bal[r] = __ballot_sync(kFull, (cand >> r) & 1u);
+            tot += __popc(bal[r]);
+        }
+        if (cnt + tot > (uint32_t)WB::kCap) wflush<kOutNode, true>(wb, ws, cnt, o);
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((bal[r] >> lane_id()) & 1u) wb.v[cnt + __popc(bal[r] & lt)] = vv[r];
+            cnt += __popc(bal[r]);
+        }
+        __syncwarp();
+        return;
+    }
     uint32_t won = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -512,7 +660,7 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
             bal[r] = __ballot_sync(kFull, (won >> r) & 1u);
             tot += __popc(bal[r]);
         }
-        if (cnt + tot > (uint32_t)kWB) wflush<kOutNode, true>(wb, ws, cnt, o);
+        if (cnt + tot > (uint32_t)WB::kCap) wflush<kOutNode, true>(wb, ws, cnt, o);
         const uint32_t lt = lanemask_lt();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -536,7 +684,7 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
     }
 #if LB_LEAN_PUSH_SIMPLE
     // flush whenever a full group might not fit, then push item by item
-    if (cnt > (uint32_t)(kWB - 32 * R)) wflush<kOutNode, true>(wb, ws, cnt, o);
+    if (cnt > (uint32_t)(WB::kCap - 32 * R)) wflush<kOutNode, true>(wb, ws, cnt, o);
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -558,7 +706,7 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
         tot += __popc(bal[r]);
     }
     if (tot == 0) return;
-    if (cnt + tot > (uint32_t)kWB) wflush<kOutNode, true>(wb, ws, cnt, o);
+    if (cnt + tot > (uint32_t)WB::kCap) wflush<kOutNode, true>(wb, ws, cnt, o);
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -571,6 +719,51 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
         cnt += __popc(bal[r]);
     }
 #endif
+    __syncwarp();
+}
+
+// SSSP relax of R loaded edges per lane with deferred atomics
+// (FlushOut::defer == 3): the plain distance check for every item, then
+// (only if some lane found an improvement) every candidate vertex and the
+// distance it offers go into the push buffer.  The flush makes the
+// atomicMin and queued-bit claims of a whole buffer at once.
+template <int R, bool COH, class WB, class WS>
+__device__ __forceinline__ void relax_sssp_defer(const bool (&ok)[R], const int32_t (&vv)[R],
+                                                 const uint32_t (&ww)[R], const uint32_t (&dd)[R],
+                                                 const uint32_t *__restrict__ status, WB &wb, WS &ws,
+                                                 uint32_t &cnt, const FlushOut &o) {
+    static_assert(R * 32 <= WB::kCap, "push buffer too small for one group");
+    uint32_t cand = 0;
+    uint32_t val[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        val[r] = 0u;
+        if (!ok[r] || dd[r] == kInf) continue;
+        // dd + w saturated at kSat: a 32-bit sum that wrapped (s < dd) or
+        // reached kSat is exactly the case of the 64-bit sum >= kSat
+        const uint32_t s32 = dd[r] + ww[r];
+        val[r] = (s32 < dd[r] || s32 >= kSat) ? kSat : s32;
+        if (val[r] < ld_mut<COH>(status + vv[r])) cand |= 1u << r;
+    }
+    if (!__any_sync(kFull, cand != 0u)) return;
+    unsigned bal[R];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        bal[r] = __ballot_sync(kFull, (cand >> r) & 1u);
+        tot += __popc(bal[r]);
+    }
+    if (cnt + tot > (uint32_t)WB::kCap) wflush<kOutNode, true>(wb, ws, cnt, o);
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if ((bal[r] >> lane_id()) & 1u) {
+            const uint32_t sl = cnt + __popc(bal[r] & lt);
+            wb.v[sl] = vv[r];
+            wb.beg[sl] = (int32_t)val[r];
+        }
+        cnt += __popc(bal[r]);
+    }
     __syncwarp();
 }
 

@@ -10,15 +10,16 @@
 
 #include "lb_device.cuh"
 
-// CTAs per SM the WD relax is compiled for (40 registers at 6), BFS and
-// SSSP.  Measured on R-MAT scale 24 with the windowed walk and 3 edges per
-// lane per round: BFS 2.08 / 2.19 / 2.48 ms at 6 / 5 / 4 CTAs, SSSP 9.37 /
-// 9.39 / 10.6 ms.
+// CTAs per SM the WD relax is compiled for (40 registers at 6, 48 at 5),
+// BFS and SSSP.  Measured on R-MAT scale 24 with the windowed walk and 3
+// edges per lane per round: BFS 2.08 / 2.19 / 2.48 ms at 6 / 5 / 4 CTAs,
+// SSSP 9.37 / 9.39 / 10.6 ms; with deferred claims BFS 1.80 / 1.86 ms at 6
+// / 5 CTAs and SSSP 7.70 / 7.52 ms.
 #ifndef LB_WD_MIN_BLOCKS
 #define LB_WD_MIN_BLOCKS 6
 #endif
 #ifndef LB_WD_MIN_BLOCKS_SSSP
-#define LB_WD_MIN_BLOCKS_SSSP 6
+#define LB_WD_MIN_BLOCKS_SSSP 5
 #endif
 // Column and weight streams loaded evict-first (ld.global.cs) so the
 // randomly read distance, queued and visited lines keep their place in L2
@@ -32,6 +33,29 @@ __device__ __forceinline__ T ld_edge(const T *p) {
     constexpr bool kStream = (LB_WD_STREAM & (SSSP ? 1 : 2)) != 0;
     return kStream ? __ldcs(p) : __ldg(p);
 }
+
+// Push-buffer entries per warp of the WD step kernel (BFS, SSSP).  The
+// shared-memory footprint decides the L1 carve-out left for the randomly
+// read visited bitmap and distances.
+#ifndef LB_KWB_WD_BFS
+#define LB_KWB_WD_BFS 128
+#endif
+#ifndef LB_KWB_WD_SSSP
+#define LB_KWB_WD_SSSP 128
+#endif
+// Deferred claims in the WD step kernel: the relax only buffers the
+// candidates that pass the plain check, and the flush makes their atomics
+// for a whole buffer at once (BFS: the visited-bit claim, FlushOut::defer
+// == 2; SSSP: the atomicMin and the queued-bit claim, defer == 3).  The
+// atomics then leave each relax group's chain of dependent accesses.
+// Measured on R-MAT scale 24, 8 sources: BFS 1.93 -> 1.80 ms, SSSP 8.47
+// -> 7.69 ms per query.
+#ifndef LB_BFS_DEFER_CLAIM
+#define LB_BFS_DEFER_CLAIM 1
+#endif
+#ifndef LB_SSSP_DEFER_CLAIM
+#define LB_SSSP_DEFER_CLAIM 1
+#endif
 
 // The final flush of a WD iteration (and of a serving RELAX tile) as one
 // list reservation per CTA (wflush_block) instead of one per warp.
@@ -272,11 +296,11 @@ __device__ __forceinline__ KT warp_search(const int32_t *scan, KT lo, KT hi, IT 
 // inside the step (an entry has at least one edge, so at most 32 start in
 // 32 positions) and takes its fields from the window by shuffle.  32-bit
 // list edges and edge ids (< 2^31, checked when the graph is created).
-template <bool SSSP, int R, bool COH>
+template <bool SSSP, int R, bool COH, class WB, class WS>
 __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
                                             int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
-                                            uint32_t *status, uint32_t level, uint32_t *err, WarpBuf &wb,
-                                            WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+                                            uint32_t *status, uint32_t level, uint32_t *err, WB &wb,
+                                            WS &ws, uint32_t &cnt, const FlushOut &o) {
     const int64_t q = T / kTileGrain;
     const int64_t W = T / kWarps;  // edges per warp and tile (a multiple of 32)
     const int64_t ntiles = (E + T - 1) / T;
@@ -399,7 +423,11 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
             }
         }
         if constexpr (SSSP) {
-            if (cnt > kWB - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
+            if (o.defer == 3) {
+                relax_sssp_defer<R, COH>(ok, vv, ww, dd, status, wb, ws, cnt, o);
+                continue;
+            }
+            if (cnt > WB::kCap - 32 * R) wflush<kOutNode, true>(wb, ws, cnt, o);
             relax_items<true, R, kOutNode, true, COH, false>(ok, vv, ww, dd, g.off, bitmap, qcur, status, level, err,
                                                              wb, ws, cnt, o);
         } else {
@@ -411,17 +439,17 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
 // One tile of the walk.  COH selects L2-coherent loads for everything other
 // CTAs write (the persistent serving and small-list kernels); the
 // single-level launches use the read-only / L1 paths.
-template <bool SSSP, int STEPS, bool COH>
+template <bool SSSP, int STEPS, bool COH, class WB, class WS>
 __device__ __forceinline__ void wd_walk_tile(const GraphDev &g, const NodeList &in, int64_t in_cnt, int64_t E,
                                              int64_t T, int64_t t, uint32_t *bitmap, uint32_t *qcur,
-                                             uint32_t *status, uint32_t level, uint32_t *err, WarpBuf &wb,
-                                             WarpScratch &ws, uint32_t &cnt, const FlushOut &o) {
+                                             uint32_t *status, uint32_t level, uint32_t *err, WB &wb,
+                                             WS &ws, uint32_t &cnt, const FlushOut &o) {
     wd_walk_win<SSSP, STEPS, COH>(g, in, in_cnt, E, T, t, bitmap, qcur, status, level, err, wb, ws, cnt, o);
 }
 
-template <bool SSSP, int STEPS>
+template <bool SSSP, int STEPS, class WB, class WS>
 __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const NodeList &in, int64_t in_cnt, int64_t E,
-                                        WarpBuf &wb, WarpScratch &ws, uint32_t &cnt, const FlushOut &o,
+                                        WB &wb, WS &ws, uint32_t &cnt, const FlushOut &o,
                                         uint32_t *status, uint32_t level, uint32_t *qcur) {
     const int64_t T = iteration_tile(E, gridDim.x, p.tile);
     const int64_t ntiles = (E + T - 1) / T;
@@ -432,8 +460,9 @@ __device__ __forceinline__ void wd_walk(const StepParams &p, Ctl *ctl, const Nod
 
 template <bool SSSP, int ITEMS>
 __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_MIN_BLOCKS) k_step_wd(StepParams p) {
-    __shared__ WarpBuf s_wb[kWarps];
-    __shared__ WarpScratch s_ws[kWarps];
+    // node pushes only: no flush scratch
+    __shared__ WarpBufT<SSSP ? LB_KWB_WD_SSSP : LB_KWB_WD_BFS> s_wb[kWarps];
+    NoScratch ns;
     Ctl *ctl = p.ctl;
     // the small-list kernel that runs before this step in the device loop
     // may have finished the query (uniform: every CTA reads the same flag)
@@ -457,14 +486,17 @@ __global__ void __launch_bounds__(kBlock, SSSP ? LB_WD_MIN_BLOCKS_SSSP : LB_WD_M
     o.err = &ctl->error;
     o.pushes = &ctl->pushes;
     o.off = p.g.off;
-    o.defer = LB_DEFER_OFFSETS;
+    o.defer = SSSP ? (LB_SSSP_DEFER_CLAIM ? 3 : LB_DEFER_OFFSETS) : (LB_BFS_DEFER_CLAIM ? 2 : LB_DEFER_OFFSETS);
+    o.claim_bitmap = SSSP ? qcur : p.bitmap;
+    o.claim_status = status;
+    o.claim_level = level;
     const uint32_t warp = threadIdx.x >> 5;
     uint32_t cnt = 0;
-    wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], s_ws[warp], cnt, o, status, level, qcur);
+    wd_walk<SSSP, ITEMS>(p, ctl, in, in_cnt, E, s_wb[warp], ns, cnt, o, status, level, qcur);
 #if LB_BLOCK_FLUSH
-    wflush_block<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
+    wflush_block<kOutNode, true>(s_wb[warp], ns, cnt, o);
 #else
-    wflush<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
+    wflush<kOutNode, true>(s_wb[warp], ns, cnt, o);
 #endif
     if (block_is_last(ctl) && threadIdx.x == 0) finish_plain_step(p, ctl, true, p.list_cap);
 }
