@@ -57,6 +57,25 @@ __device__ __forceinline__ T ld_edge(const T *p) {
 #define LB_SSSP_DEFER_CLAIM 1
 #endif
 
+// Runs through long adjacency lists: after the first group of a run, the
+// following groups of the same entry skip the window and bounds work, and
+// (SSSP) a run of a stale entry is skipped whole (bit mask: 1 = SSSP, 2 =
+// BFS).  Measured on R-MAT scale 24 with the bitmap at one address: SSSP
+// 6.64 -> 6.16 ms per query, BFS 1% to 3% slower (not used).
+#ifndef LB_WD_RUN_LOOP
+#define LB_WD_RUN_LOOP 1
+#endif
+template <bool SSSP>
+__host__ __device__ constexpr bool wd_run_loop() {
+    return (LB_WD_RUN_LOOP & (SSSP ? 1 : 2)) != 0;
+}
+// SSSP: the walk skips the loads of entries whose vertex was queued again
+// in this iteration (they relax nothing: the next iteration expands them).
+// Measured on R-MAT scale 24: SSSP 7.38 -> 6.64 ms per query.
+#ifndef LB_SSSP_SKIP_STALE
+#define LB_SSSP_SKIP_STALE 1
+#endif
+
 // The final flush of a WD iteration (and of a serving RELAX tile) as one
 // list reservation per CTA (wflush_block) instead of one per warp.
 #ifndef LB_BLOCK_FLUSH
@@ -341,10 +360,29 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
     load(kb + (int32_t)lane, s0, d0, u0);
     load(kb + 32 + (int32_t)lane, s1, d1, u1);
     int32_t ew = w0;
+    // the run in progress (wd_run_loop): its CSR delta, the list edge where
+    // its entry ends and where the warp's slice or the entry ends (0:
+    // none), and (SSSP) the distance it relaxes with
+    int32_t run_d = 0, run_next = 0, run_end = 0;
+    uint32_t run_du = 0u;
     while (ew < w1) {  // warp-uniform
         bool ok[R];
         int32_t vv[R];
         uint32_t ww[R], dd[R];
+        if (wd_run_loop<SSSP>() && ew + 32 * R <= run_end) {
+            // a further group of the run: no window or bounds work
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int32_t e = ew + 32 * r + (int32_t)lane;
+                ok[r] = true;
+                vv[r] = ld_edge<SSSP>(g.col + (run_d + e));
+                ww[r] = SSSP ? ld_edge<SSSP>(g.w + (run_d + e)) : 0u;
+                dd[r] = SSSP ? run_du : 0u;
+            }
+            ew += 32 * R;
+            if (run_next == ew) kcur += 1;
+            goto relax_group;
+        }
         if (kcur >= kb + 32) {  // slide: the second half becomes the first
             kb += 32;
             s0 = s1;
@@ -352,6 +390,7 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
             u0 = u1;
             load(kb + 32 + (int32_t)lane, s1, d1, u1);
         }
+        {
         // start of entry kcur + 1 (window position 1..32)
         const int32_t pn = kcur + 1 - kb;
         const int32_t s_next = __shfl_sync(kFull, pn < 32 ? s0 : s1, pn & 31);
@@ -360,14 +399,32 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
             const int32_t pc = kcur - kb;
             const int32_t dcur = __shfl_sync(kFull, d0, pc);
             const uint32_t ducur = SSSP ? __shfl_sync(kFull, u0, pc) : 0u;
-            if (dcur + ew < 0 || dcur + min(ew + 32 * R, w1) > m) {
+            if (wd_run_loop<SSSP>()) {
+                // the whole run is checked once
+                if (dcur + ew < 0 || dcur + min(s_next, w1) > m) {
+                    if (lane == 0) atomicOr(err, kErrBounds);
+                    return;
+                }
+                if (SSSP && LB_SSSP_SKIP_STALE && ducur == kInf) {
+                    // queued again in this iteration: the entry relaxes nothing
+                    ew = min(s_next, w1);
+                    if (s_next == ew) kcur += 1;
+                    continue;
+                }
+                run_d = dcur;
+                run_next = s_next;
+                run_end = min(s_next, w1);
+                if (SSSP) run_du = ducur;
+            } else if (dcur + ew < 0 || dcur + min(ew + 32 * R, w1) > m) {
                 if (lane == 0) atomicOr(err, kErrBounds);
                 return;
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int32_t e = ew + 32 * r + (int32_t)lane;
-                ok[r] = e < w1;
+                // SSSP: an entry queued again in this iteration (ducur =
+                // kInf) relaxes nothing; its edges are not loaded
+                ok[r] = e < w1 && (!SSSP || !LB_SSSP_SKIP_STALE || ducur != kInf);
                 vv[r] = ok[r] ? ld_edge<SSSP>(g.col + (dcur + e)) : 0;
                 ww[r] = (SSSP && ok[r]) ? ld_edge<SSSP>(g.w + (dcur + e)) : 0u;
                 dd[r] = ducur;
@@ -405,7 +462,7 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
                 }
                 const int32_t e = ew + (int32_t)lane;
                 const int32_t eidx = (pe < 32 ? x0 : x1) + e;
-                if (e < w1) {
+                if (e < w1 && (!SSSP || !LB_SSSP_SKIP_STALE || du != kInf)) {
                     if ((uint32_t)eidx >= (uint32_t)m) {
                         atomicOr(err, kErrBounds);
                     } else {
@@ -422,6 +479,8 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
                 ew += 32;
             }
         }
+        }
+    relax_group:
         if constexpr (SSSP) {
             if (o.defer == 3) {
                 relax_sssp_defer<R, COH>(ok, vv, ww, dd, status, wb, ws, cnt, o);
