@@ -131,7 +131,16 @@ typedef struct lb_options {
                               grid barrier, so the other CTAs' bounded waits
                               run out (2 s) and the query returns
                               LB_ERR_TIMEOUT with the device still usable */
-    int32_t reserved[3];
+    int32_t bitmap_place;  /* 0..7 (0): where the visited / queued bitmap
+                              starts inside its allocation, in steps of
+                              min(1 MiB, one bitmap half rounded up to 4
+                              KiB).  The bitmap is small and read at random
+                              by every SM, and on GB300 the time of a BFS
+                              depends on where its lines fall (R-MAT scale
+                              24: 1.80 to 1.94 ms per query over eight
+                              placements); lb_autotune picks the fastest.
+                              The allocation carries the 7 steps of slack. */
+    int32_t reserved[2];
 } lb_options;
 
 /* Device bytes by structure (lb_mem_report).  "extra" is everything a
@@ -264,8 +273,9 @@ lb_status lb_release_workspaces(lb_graph *g);
  * 4096 edges; NS -- the granule size (MDT from the histogram, or 32 / 256 /
  * 2048) in the paper's form, and the binned form with the histogram MDT or
  * 256 / 2048 x thread bin 8 / 32 / 128; NS_PHYS -- the granule size; BS, EP
- * -- CTAs per SM.  Fields outside the grid keep their values.  On any
- * failure the options in force before the call are restored. */
+ * -- CTAs per SM.  Then, with the fastest of these, the eight bitmap
+ * placements (bitmap_place).  Fields outside the grid keep their values.
+ * On any failure the options in force before the call are restored. */
 lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *srcs, int32_t nsrc, lb_options *best,
                       double *best_ms);
 

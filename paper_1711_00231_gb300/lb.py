@@ -39,7 +39,8 @@ class lb_options(ctypes.Structure):
                 ("loop_mode", ctypes.c_int32), ("wd_tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("hp_mode", ctypes.c_int32), ("hp_warp_max", ctypes.c_int32), ("ns_mode", ctypes.c_int32),
                 ("thread_max", ctypes.c_int32), ("hp_depth", ctypes.c_int32), ("small_edges", ctypes.c_int32),
-                ("test_barrier_skip", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("test_barrier_skip", ctypes.c_int32), ("bitmap_place", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class lb_mem_stats(ctypes.Structure):

@@ -48,9 +48,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lb_options), sizeof(lb_mem_stats), sizeof(lb_query_stats), sizeof(lb_step_record));
   printf("%zu %zu %zu %zu\n", offsetof(lb_query_stats, status), offsetof(lb_query_stats, device_ms), offsetof(lb_mem_stats, ns_split), offsetof(lb_step_record, t_ns));
   printf("%zu %zu %zu %zu\n", sizeof(lb_server_state_t), sizeof(lb_slot_state_t), offsetof(lb_server_state_t, slot), offsetof(lb_slot_state_t, ticket));
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", offsetof(lb_options, hp_mode), offsetof(lb_options, hp_warp_max),
          offsetof(lb_options, ns_mode), offsetof(lb_options, thread_max), offsetof(lb_options, hp_depth),
-         offsetof(lb_options, small_edges), sizeof(lb_options));
+         offsetof(lb_options, small_edges), offsetof(lb_options, bitmap_place), sizeof(lb_options));
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(lb_server_options, mem_fraction), offsetof(lb_server_options, launch_ms),
          offsetof(lb_server_options, policy), sizeof(lb_server_options), offsetof(lb_server_info_t, pending),
          sizeof(lb_server_info_t));
@@ -70,7 +70,7 @@ int main(void) {
     assert [int(x) for x in d.split()] == [lb.lb_options.hp_mode.offset, lb.lb_options.hp_warp_max.offset,
                                            lb.lb_options.ns_mode.offset, lb.lb_options.thread_max.offset,
                                            lb.lb_options.hp_depth.offset, lb.lb_options.small_edges.offset,
-                                           ctypes.sizeof(lb.lb_options)]
+                                           lb.lb_options.bitmap_place.offset, ctypes.sizeof(lb.lb_options)]
     assert [int(x) for x in e.split()] == [lb.lb_server_options.mem_fraction.offset,
                                            lb.lb_server_options.launch_ms.offset, lb.lb_server_options.policy.offset,
                                            ctypes.sizeof(lb.lb_server_options), lb.lb_server_info_t.pending.offset,

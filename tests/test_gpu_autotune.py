@@ -40,6 +40,7 @@ def test_autotune_returns_grid_options_and_exact_results(strategy):
         assert ms > 0
         for field, values in GRID[strategy].items():
             assert best[field] in values, (strategy, field, best[field])
+        assert best["bitmap_place"] in range(8)  # the placement pass after the grid
         assert G.options() == best
         if strategy == "HP" and best["hp_mode"] == 1:
             assert best["thread_max"] in {8, 32, 128} and best["hp_warp_max"] in {512, 4096}

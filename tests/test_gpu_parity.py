@@ -119,13 +119,30 @@ def test_ns_binned_granules_match_oracle(opts):
         run_all(g, srcs, strategies=["NS"], options=opts)
 
 
+def test_bitmap_placements_match_oracle():
+    # the bitmap starts bitmap_place steps into its allocation (step = one
+    # half rounded up to 4 KiB, at most 1 MiB): every placement, every
+    # strategy, both kinds, exact; the visited bytes include the slack
+    for g, srcs in [(gg.rmat(14, 16, seed=1), [0, 17]), (gg.grid(64, 48, seed=3), [0])]:
+        for place in range(8):
+            run_all(g, srcs, options=dict(bitmap_place=place))
+        words = ((g.n + 31) // 32 + 3) // 4 * 4
+        step = min((words + 1023) // 1024 * 1024, 1 << 18)
+        G = lb.Graph.from_csr(g)
+        try:
+            assert G.mem_report("WD")["visited"] == 4 * (2 * words + 7 * step)
+        finally:
+            G.close()
+
+
 def test_option_validation():
     g = gg.rmat(10, 8, seed=1)
     G = lb.Graph.from_csr(g)
     try:
         for bad in [dict(hp_mode=2), dict(hp_warp_max=16), dict(wd_tile=300), dict(wd_tile=65536), dict(loop_mode=3),
                     dict(hist_bins=5000), dict(ctas_per_sm=40), dict(ns_mode=2), dict(thread_max=2000),
-                    dict(thread_max=-1), dict(hp_depth=9), dict(hp_depth=-2)]:
+                    dict(thread_max=-1), dict(hp_depth=9), dict(hp_depth=-2), dict(bitmap_place=8),
+                    dict(bitmap_place=-1)]:
             with pytest.raises(lb.LbError):
                 G.set_options(**bad)
         G.set_options(hp_mode=1, hp_warp_max=64)
