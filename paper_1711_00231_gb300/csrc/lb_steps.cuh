@@ -76,6 +76,13 @@ __host__ __device__ constexpr bool wd_run_loop() {
 #define LB_SSSP_SKIP_STALE 1
 #endif
 
+// Deferred claims in the persistent small-list kernel (as in the WD step;
+// bit mask: 1 = SSSP, 2 = BFS).  Measured on the 4096^2 grid: BFS equal,
+// SSSP 2% slower with them (408 -> 416 ms), so BFS only.
+#ifndef LB_SMALL_DEFER_CLAIM
+#define LB_SMALL_DEFER_CLAIM 2
+#endif
+
 // The final flush of a WD iteration (and of a serving RELAX tile) as one
 // list reservation per CTA (wflush_block) instead of one per warp.
 #ifndef LB_BLOCK_FLUSH
@@ -622,8 +629,9 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, bool *stop) {
 #endif
 template <bool SSSP, int ITEMS>
 __global__ void __launch_bounds__(kBlock, LB_SMALL_CTAS) k_small_levels(StepParams p) {
+    // node pushes only: no flush scratch
     __shared__ WarpBuf s_wb[kWarps];
-    __shared__ WarpScratch s_ws[kWarps];
+    NoScratch ns;
     Ctl *ctl = p.ctl;
     const int64_t lim = p.small_edges;
     uint32_t level = *(volatile uint32_t *)&ctl->level;
@@ -667,14 +675,18 @@ __global__ void __launch_bounds__(kBlock, LB_SMALL_CTAS) k_small_levels(StepPara
         o.pushes = &ctl->pushes;
         o.child_first = nullptr;
         o.off = p.g.off;
-        o.defer = LB_DEFER_OFFSETS;
+        o.defer = SSSP ? ((LB_SMALL_DEFER_CLAIM & 1) ? 3 : LB_DEFER_OFFSETS)
+                       : ((LB_SMALL_DEFER_CLAIM & 2) ? 2 : LB_DEFER_OFFSETS);
+        o.claim_bitmap = SSSP ? qcur : p.bitmap;
+        o.claim_status = status;
+        o.claim_level = level;
         uint32_t cnt = 0;
         const int64_t T = iteration_tile(E, gridDim.x, p.tile);
         const int64_t ntiles = (E + T - 1) / T;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
             wd_walk_tile<SSSP, ITEMS, true>(p.g, in, in_cnt, E, T, t, p.bitmap, qcur, status, level, &ctl->error,
-                                            s_wb[warp], s_ws[warp], cnt, o);
-        wflush_block<kOutNode, true>(s_wb[warp], s_ws[warp], cnt, o);
+                                            s_wb[warp], ns, cnt, o);
+        wflush_block<kOutNode, true>(s_wb[warp], ns, cnt, o);
         // test hook: one CTA that never arrives makes the others' waits run out
         if (p.test_barrier_skip && blockIdx.x == 1) return;
         bool stop = false;
