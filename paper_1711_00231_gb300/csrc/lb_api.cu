@@ -1031,7 +1031,21 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
             best_o = o;
         }
     }
-    // then where the bitmap lies, with the fastest options
+    // then where the bitmap lies, with the fastest options; and for WD
+    // whether the persistent small-list launch is worth its conditional
+    // node (a few microseconds per level on graphs that never run it)
+    if (best_t < 1e300 && s == LB_WD && best_o.small_edges != 0) {
+        lb_options o = best_o;
+        o.small_edges = 0;
+        bool ok = false;
+        double tot = 0.0;
+        const lb_status st = time_opts(o, &ok, &tot);
+        if (st != LB_OK) return restore(st);
+        if (ok && tot < best_t) {
+            best_t = tot;
+            best_o = o;
+        }
+    }
     if (best_t < 1e300) {
         const lb_options grid_best = best_o;
         for (int32_t pl = 0; pl < kBitmapPlaces; ++pl) {

@@ -722,6 +722,12 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
     __syncwarp();
 }
 
+// SSSP distance checks of the deferred relax through L2 (1) or L1 (0): the
+// distance array is read at random and L1 hits are rare (11-14% at R-MAT
+// scale 22).  Measured on R-MAT scale 24: SSSP 1.6-1.7% faster through L2.
+#ifndef LB_SSSP_STATUS_CG
+#define LB_SSSP_STATUS_CG 1
+#endif
 // SSSP relax of R loaded edges per lane with deferred atomics
 // (FlushOut::defer == 3): the plain distance check for every item, then
 // (only if some lane found an improvement) every candidate vertex and the
@@ -743,7 +749,7 @@ __device__ __forceinline__ void relax_sssp_defer(const bool (&ok)[R], const int3
         // reached kSat is exactly the case of the 64-bit sum >= kSat
         const uint32_t s32 = dd[r] + ww[r];
         val[r] = (s32 < dd[r] || s32 >= kSat) ? kSat : s32;
-        if (val[r] < ld_mut<COH>(status + vv[r])) cand |= 1u << r;
+        if (val[r] < ld_mut<COH || LB_SSSP_STATUS_CG>(status + vv[r])) cand |= 1u << r;
     }
     if (!__any_sync(kFull, cand != 0u)) return;
     unsigned bal[R];

@@ -41,6 +41,8 @@ def test_autotune_returns_grid_options_and_exact_results(strategy):
         for field, values in GRID[strategy].items():
             assert best[field] in values, (strategy, field, best[field])
         assert best["bitmap_place"] in range(8)  # the placement pass after the grid
+        if strategy == "WD":  # the small-list pass: the default threshold or off
+            assert best["small_edges"] in {0, 16384}
         assert G.options() == best
         if strategy == "HP" and best["hp_mode"] == 1:
             assert best["thread_max"] in {8, 32, 128} and best["hp_warp_max"] in {512, 4096}
@@ -50,6 +52,22 @@ def test_autotune_returns_grid_options_and_exact_results(strategy):
             assert np.array_equal(G.bfs(src, strategy), oracle.bfs(g, src)[0])
             d, rc = G.sssp(src, strategy)
             assert rc == lb.LB_OK and np.array_equal(d, oracle.dijkstra(g, src)[0])
+    finally:
+        G.close()
+
+
+def test_autotune_keeps_the_small_list_launch_on_a_grid():
+    # a 256 x 256 grid has 511 BFS levels of at most a few hundred edges:
+    # the persistent small-list launch (a grid barrier per level) beats a
+    # launch per level by far, so the tuner must keep it on
+    g = gg.grid(256, 256, seed=1)
+    G = lb.Graph.from_csr(g)
+    try:
+        best, ms = G.autotune("both", "WD", [0])
+        assert best["small_edges"] > 0, best
+        assert np.array_equal(G.bfs(0, "WD"), oracle.bfs(g, 0)[0])
+        d, rc = G.sssp(0, "WD")
+        assert rc == lb.LB_OK and np.array_equal(d, oracle.dijkstra(g, 0)[0])
     finally:
         G.close()
 
