@@ -1,13 +1,17 @@
 // Device building blocks shared by the step kernels of every strategy.
 //
-//  * Relax ops (the paper's Algorithms for EP and WD: "altdist =
-//    dist[src] + weight; if dist[dst] > altdist: update dist, push dst"):
+//  * Relax ops (the relaxation of the paper's EP and WD algorithms: a
+//    destination whose distance exceeds the source's distance plus the
+//    edge weight takes that sum and is pushed):
 //      BFS  - claim v with atomicOr on a visited bitmap, level[v] = L + 1;
 //      SSSP - atomicMin on dist[v]; queue v only for the first improvement
 //             in an iteration (atomicOr on the iteration's queued bitmap),
 //             so a list never exceeds n.
 //    Both run test-then-atomic: the plain read can only be stale in the
 //    direction that costs an extra atomic, never one that loses an update.
+//    In the WD kernels the atomics are deferred: the relax buffers the
+//    candidates that pass the plain test, and the flush makes the atomics
+//    of a whole buffer at once (FlushOut::defer).
 //  * Warp push buffers: the paper pushes with one atomic per node ("work
 //    chunking", Sec. II-B / IV-D).  Here a warp collects up to kWB pushed
 //    nodes in shared memory and reserves their list slots and their edges
