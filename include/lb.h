@@ -443,7 +443,9 @@ lb_status lb_server_stop(lb_server *s);
  * nothing.  Limits: n <= 131072
  * and m <= 16777216; larger sizes return LB_ERR_ARG.  The first call on a
  * device looks the array up (cudaGetSymbolAddress) and should come before
- * any stream capture.  Every call shares the array; calls whose GPU work
+ * any stream capture.  The address is kept for the life of the process: a
+ * process that resets the device (cudaDeviceReset) must not call this
+ * entry point on that device afterwards.  Every call shares the array; calls whose GPU work
  * overlaps race and give wrong results.  The call waits for its result on
  * `stream` (it reads the worklist size back every iteration). */
 lb_status lb_bfs_wd_noalloc(const int64_t *offsets_dev, const int32_t *cols_dev, int64_t n, int64_t m, int32_t src,
