@@ -6,7 +6,7 @@
 namespace lbk {
 
 cudaError_t launch_step_wd(bool sssp, const StepParams &p, int grid, cudaStream_t st) {
-    if (sssp) k_step_wd<true, kItemsWd><<<grid, kBlock, 0, st>>>(p);
+    if (sssp) k_step_wd<true, kItemsWdSssp><<<grid, kBlock, 0, st>>>(p);
     else k_step_wd<false, kItemsWdBfs><<<grid, kBlock, 0, st>>>(p);
     return cudaGetLastError();
 }
@@ -32,7 +32,7 @@ int small_ctas_per_sm() { return LB_SMALL_CTAS; }
 
 int occupancy_step_wd(bool sssp) {
     int nb = 0;
-    cudaError_t e = sssp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_wd<true, kItemsWd>, kBlock, 0)
+    cudaError_t e = sssp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_wd<true, kItemsWdSssp>, kBlock, 0)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_wd<false, kItemsWdBfs>, kBlock, 0);
     return (e == cudaSuccess && nb > 0) ? nb : 1;
 }

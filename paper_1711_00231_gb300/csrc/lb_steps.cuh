@@ -10,16 +10,17 @@
 
 #include "lb_device.cuh"
 
-// CTAs per SM the WD relax is compiled for (40 registers at 6, 48 at 5),
-// BFS and SSSP.  Measured on R-MAT scale 24 with the windowed walk and 3
-// edges per lane per round: BFS 2.08 / 2.19 / 2.48 ms at 6 / 5 / 4 CTAs,
-// SSSP 9.37 / 9.39 / 10.6 ms; with deferred claims BFS 1.80 / 1.86 ms at 6
-// / 5 CTAs and SSSP 7.70 / 7.52 ms.
+// CTAs per SM the WD relax is compiled for (40 registers at 6, 48 at 5,
+// 64 at 4), BFS and SSSP.  Measured on R-MAT scale 24 with the windowed
+// walk and 3 edges per lane per round: BFS 2.08 / 2.19 / 2.48 ms at 6 / 5 /
+// 4 CTAs, SSSP 9.37 / 9.39 / 10.6 ms; with deferred claims BFS 1.80 / 1.86
+// ms at 6 / 5 CTAs and SSSP 7.70 / 7.52 ms.  SSSP now takes 4 edges per lane
+// at 4 CTAs (6.70 -> 6.58 ms against 3 edges at 5 CTAs).
 #ifndef LB_WD_MIN_BLOCKS
 #define LB_WD_MIN_BLOCKS 6
 #endif
 #ifndef LB_WD_MIN_BLOCKS_SSSP
-#define LB_WD_MIN_BLOCKS_SSSP 5
+#define LB_WD_MIN_BLOCKS_SSSP 4
 #endif
 // Column and weight streams loaded evict-first (ld.global.cs) so the
 // randomly read distance, queued and visited lines keep their place in L2
@@ -32,6 +33,30 @@ template <bool SSSP, class T>
 __device__ __forceinline__ T ld_edge(const T *p) {
     constexpr bool kStream = (LB_WD_STREAM & (SSSP ? 1 : 2)) != 0;
     return kStream ? __ldcs(p) : __ldg(p);
+}
+
+// 16-byte column / weight loads (bit mask: 1 = SSSP, 2 = BFS): with 4 edges
+// per lane per group, a group that lies inside one adjacency list is read
+// as one 16-byte load per lane and array (lane l takes the group's edges
+// 4l .. 4l + 3).  A group starting off a 16-byte boundary is loaded from
+// the boundary below with its first 1-3 edges masked, after which the rest
+// of the list is aligned.  Used only when the arrays start on 16-byte
+// boundaries (a custom allocator may return other addresses).
+#ifndef LB_WD_VEC
+#define LB_WD_VEC 0
+#endif
+template <bool SSSP, int R>
+__host__ __device__ constexpr bool wd_vec() {
+    return R == 4 && (LB_WD_VEC & (SSSP ? 1 : 2)) != 0;
+}
+template <bool SSSP, class T>
+__device__ __forceinline__ uint4 ld_edge4(const T *p) {
+    constexpr bool kStream = (LB_WD_STREAM & (SSSP ? 1 : 2)) != 0;
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    return kStream ? __ldcs(q) : __ldg(q);
+}
+__device__ __forceinline__ uint32_t u4_get(const uint4 &x, int r) {
+    return r == 0 ? x.x : r == 1 ? x.y : r == 2 ? x.z : x.w;
 }
 
 // Push-buffer entries per warp of the WD step kernel (BFS, SSSP).  The
@@ -364,6 +389,9 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
     const int32_t w1 = (int32_t)min(w064 + W, e1);
     const int32_t ihiK = (int32_t)ihi;
     const int32_t m = (int32_t)g.m;
+    const bool vec_ok = wd_vec<SSSP, R>() &&
+                        ((reinterpret_cast<uintptr_t>(g.col) | (SSSP ? reinterpret_cast<uintptr_t>(g.w) : 0u)) &
+                         15u) == 0;
     int32_t kcur;
     if (on_grain) {
         if (kg < (int32_t)i0 || kg >= ihiK) {
@@ -404,6 +432,21 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
         uint32_t ww[R], dd[R];
         if (wd_run_loop<SSSP>() && ew + 32 * R <= run_end) {
             // a further group of the run: no window or bounds work
+            if (wd_vec<SSSP, R>() && vec_ok && ((run_d + ew) & 3) == 0) {
+                const int32_t a = run_d + ew + 4 * (int32_t)lane;
+                const uint4 c4 = ld_edge4<SSSP>(g.col + a);
+                const uint4 w4 = SSSP ? ld_edge4<SSSP>(g.w + a) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    ok[r] = true;
+                    vv[r] = (int32_t)u4_get(c4, r);
+                    ww[r] = u4_get(w4, r);
+                    dd[r] = SSSP ? run_du : 0u;
+                }
+                ew += 32 * R;
+                if (run_next == ew) kcur += 1;
+                goto relax_group;
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int32_t e = ew + 32 * r + (int32_t)lane;
@@ -451,6 +494,32 @@ __device__ __forceinline__ void wd_walk_win(const GraphDev &g, const NodeList &i
             } else if (dcur + ew < 0 || dcur + min(ew + 32 * R, w1) > m) {
                 if (lane == 0) atomicOr(err, kErrBounds);
                 return;
+            }
+            if (wd_vec<SSSP, R>() && vec_ok && ew + 32 * R <= w1) {
+                // 16-byte loads from the boundary at or below the group's
+                // first edge; the h edges before it are masked and the
+                // group takes 32 R - h edges (so later groups are aligned).
+                // [dcur + ew - h, dcur + ew + 32 R - h) lies inside the
+                // checked range [dcur + ew, dcur + w1) widened by h < 4
+                // edges of this list's predecessors, all below m.
+                const int32_t h = (dcur + ew) & 3;
+                const int32_t a = dcur + ew - h + 4 * (int32_t)lane;
+                const bool live = !SSSP || !LB_SSSP_SKIP_STALE || ducur != kInf;
+                uint4 c4 = make_uint4(0u, 0u, 0u, 0u), w4 = make_uint4(0u, 0u, 0u, 0u);
+                if (live) {
+                    c4 = ld_edge4<SSSP>(g.col + a);
+                    if (SSSP) w4 = ld_edge4<SSSP>(g.w + a);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    ok[r] = live && 4 * (int32_t)lane + r >= h;
+                    vv[r] = (int32_t)u4_get(c4, r);
+                    ww[r] = u4_get(w4, r);
+                    dd[r] = ducur;
+                }
+                ew += 32 * R - h;
+                if (s_next == ew) kcur += 1;
+                goto relax_group;
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
