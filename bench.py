@@ -684,27 +684,44 @@ def main():
         extra["configs"] = small_configs(torch)
         extra["grid4096"] = grid_bench(torch)
 
-    # end to end through the host-buffer C-ABI calls (lb_bfs / lb_sssp):
-    # includes the D2H copy of every result into pinned host memory
+    # end to end through the host-buffer C-ABI calls: every result is copied
+    # into pinned host memory inside the timed region.  The batched calls
+    # (lb_bfs_batch / lb_sssp_batch: one call per kind over all sources)
+    # copy query i's result while query i + 1 runs; the one-query calls
+    # (lb_bfs / lb_sssp) are timed beside them
     e2e = None
     if rank == 0:
         host = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
         hostu = host.view(np.uint32)
+        hb_t = torch.empty(len(srcs) * n, dtype=torch.int32, pin_memory=True)
+        hb = hb_t.numpy()
+        hbu = hb.view(np.uint32)
+        src_list = [int(s) for s in srcs]
         G.bfs(int(srcs[0]), strat)  # warm
+        lb.lb_bfs_batch(G.h, src_list[:2], strat, hb[:2 * n])  # warm (second result buffer, copy stream)
+        e_done = sum(work[(kind, s)][0] for kind in kinds for s in src_list)
         t0 = time.perf_counter()
-        e_done = 0
         for kind in kinds:
-            for s in srcs:
-                if kind == "bfs":
-                    lb.lb_bfs(G.h, int(s), strat, host)
-                else:
-                    lb.lb_sssp(G.h, int(s), strat, hostu)
-                e_done += work[(kind, int(s))][0]
+            if kind == "bfs":
+                lb.lb_bfs_batch(G.h, src_list, strat, hb)
+            else:
+                lb.lb_sssp_batch(G.h, src_list, strat, hbu)
         dt = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for kind in kinds:
+            for s in src_list:
+                if kind == "bfs":
+                    lb.lb_bfs(G.h, s, strat, host)
+                else:
+                    lb.lb_sssp(G.h, s, strat, hostu)
+        dt1 = time.perf_counter() - t0
         e2e = {"value": e_done / dt / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs) * len(kinds),
                "d2h_bytes_per_step": 4 * n * len(srcs) * len(kinds),
-               "note": "graph resident; per query the source id goes in as a launch argument and the n x 4 B "
-                       "result comes back to pinned host memory"}
+               "call": "lb_bfs_batch / lb_sssp_batch (all sources of a kind in one call)",
+               "one_query_calls": {"value": e_done / dt1 / 1e9, "unit": "GTEPS", "call": "lb_bfs / lb_sssp"},
+               "note": "graph resident; the source ids go in as host arguments and every n x 4 B result comes "
+                       "back to pinned host memory (host-timed, wall clock)"}
+        del hb, hbu, hb_t
 
     batched = None
     if rank == 0 and not args.no_serve:

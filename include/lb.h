@@ -234,6 +234,24 @@ lb_status lb_bfs(lb_graph *g, int32_t src, lb_strategy s, int32_t *levels_out);
  * weighted graph (LB_ERR_UNSUPPORTED otherwise). */
 lb_status lb_sssp(lb_graph *g, int32_t src, lb_strategy s, uint32_t *dist_out);
 
+/* k host-output queries from srcs[0..k-1] (the paper's problem statement,
+ * as for lb_bfs / lb_sssp, once per source).  out: host array of k * n
+ * elements; the result of query i goes to out[i * n .. i * n + n - 1] (same
+ * values and conventions as lb_bfs / lb_sssp).  Query i + 1 runs on the
+ * device while the result of query i is copied to the host: the results
+ * alternate between two device buffers of n words (the second one is held
+ * with the workspaces until lb_release_workspaces) and the copies run on a
+ * stream of their own, so with pinned host memory (cudaMallocHost or
+ * cudaHostRegister) the copies overlap the traversals; with pageable memory
+ * the results are the same but the copies serialise.  Every source is
+ * checked before anything runs (LB_ERR_ARG).  The call returns once every
+ * result is on the host, with LB_OK or the status of the first query that
+ * failed (lb_last_error names it; SSSP: LB_ERR_OVERFLOW as in lb_sssp, the
+ * other results still written).  lb_last_stats / lb_last_trace then
+ * describe the last query.  k = 0 does nothing. */
+lb_status lb_bfs_batch(lb_graph *g, const int32_t *srcs, int64_t k, lb_strategy s, int32_t *levels_out);
+lb_status lb_sssp_batch(lb_graph *g, const int32_t *srcs, int64_t k, lb_strategy s, uint32_t *dist_out);
+
 /* Device-output forms.  out_dev: n int32 (BFS levels) or n uint32 (SSSP
  * distances) on the graph's device; parents_dev: NULL or n int32 receiving
  * a shortest-path tree (parent[src] = src, -1 unreachable; the parent of v

@@ -125,6 +125,8 @@ def _load():
         "lb_get_options": ([P, ctypes.POINTER(lb_options)], st),
         "lb_bfs": ([P, i32, st, P], st),
         "lb_sssp": ([P, i32, st, P], st),
+        "lb_bfs_batch": ([P, P, i64, st, P], st),
+        "lb_sssp_batch": ([P, P, i64, st, P], st),
         "lb_bfs_dev": ([P, i32, st, P, P, P], st),
         "lb_sssp_dev": ([P, i32, st, P, P, P], st),
         "lb_last_stats": ([P, ctypes.POINTER(lb_query_stats)], st),
@@ -270,6 +272,33 @@ def lb_bfs(g: int, src: int, strategy, levels_out: np.ndarray) -> int:
 def lb_sssp(g: int, src: int, strategy, dist_out: np.ndarray) -> int:
     """Host-output SSSP; returns LB_OK or LB_ERR_OVERFLOW, raises otherwise."""
     rc = _load().lb_sssp(g, src, _strategy(strategy), _ptr(dist_out))
+    if rc not in (LB_OK, LB_ERR_OVERFLOW):
+        _check(rc)
+    return rc
+
+
+def _sources(srcs) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(srcs, dtype=np.int64))
+    if a.ndim != 1 or (a.size and (a.min() < -(1 << 31) or a.max() >= (1 << 31))):
+        raise ValueError("sources must be a 1-D sequence of int32 vertex ids")
+    return a.astype(np.int32)
+
+
+def lb_bfs_batch(g: int, srcs, strategy, levels_out: np.ndarray) -> int:
+    """Host-output BFS from every source (results row by row in levels_out,
+    k x n int32); returns the lb_status (raises on other errors)."""
+    a = _sources(srcs)
+    rc = _load().lb_bfs_batch(g, _ptr(a), a.size, _strategy(strategy), _ptr(levels_out))
+    if rc != LB_OK:
+        _check(rc)
+    return rc
+
+
+def lb_sssp_batch(g: int, srcs, strategy, dist_out: np.ndarray) -> int:
+    """Host-output SSSP from every source (k x n uint32); returns LB_OK or
+    LB_ERR_OVERFLOW, raises otherwise."""
+    a = _sources(srcs)
+    rc = _load().lb_sssp_batch(g, _ptr(a), a.size, _strategy(strategy), _ptr(dist_out))
     if rc not in (LB_OK, LB_ERR_OVERFLOW):
         _check(rc)
     return rc
@@ -497,6 +526,26 @@ class Graph:
     def sssp(self, src: int, strategy="WD"):
         out = np.empty(self.n, dtype=np.uint32)
         rc = lb_sssp(self.h, src, strategy, out)
+        return out, rc
+
+    def _batch_out(self, srcs, out, dtype):
+        k = len(srcs)
+        if out is None:
+            out = np.empty((k, self.n), dtype=dtype)
+        if not isinstance(out, np.ndarray) or out.dtype != dtype or out.size != k * self.n:
+            raise ValueError(f"output must be a {dtype.__name__} array of {k} x {self.n} elements")
+        return out
+
+    def bfs_batch(self, srcs, strategy="WD", out=None) -> np.ndarray:
+        """Levels from every source, one row per source (pass pinned host
+        memory as out to overlap the copies with the traversals)."""
+        out = self._batch_out(srcs, out, np.int32)
+        lb_bfs_batch(self.h, srcs, strategy, out)
+        return out
+
+    def sssp_batch(self, srcs, strategy="WD", out=None):
+        out = self._batch_out(srcs, out, np.uint32)
+        rc = lb_sssp_batch(self.h, srcs, strategy, out)
         return out, rc
 
     def bfs_dev(self, src, strategy, out_dev, parents_dev=None, stream=None):

@@ -105,6 +105,9 @@ def test_argument_errors_need_no_gpu():
     assert L.lb_graph_destroy(None) == lb.LB_OK
     assert L.lb_bfs(None, 0, 0, None) == lb.LB_ERR_ARG
     assert L.lb_sssp_dev(None, 0, 0, None, None, None) == lb.LB_ERR_ARG
+    srcs = np.zeros(2, dtype=np.int32)
+    assert L.lb_bfs_batch(None, srcs.ctypes.data, 2, 0, None) == lb.LB_ERR_ARG
+    assert L.lb_sssp_batch(None, srcs.ctypes.data, 2, 0, None) == lb.LB_ERR_ARG
     st = lb.lb_query_stats()
     assert L.lb_last_stats(None, ctypes.byref(st)) == lb.LB_ERR_ARG
     ms = lb.lb_mem_stats()
