@@ -728,9 +728,11 @@ __device__ __forceinline__ void relax_bfs_lean(const bool (&ok)[R], const int32_
 
 // SSSP distance checks of the deferred relax through L2 (1) or L1 (0): the
 // distance array is read at random and L1 hits are rare (11-14% at R-MAT
-// scale 22).  Measured on R-MAT scale 24: SSSP 1.6-1.7% faster through L2.
+// scale 22).  Measured on R-MAT scale 24: with 3 edges per lane at 5 CTAs
+// per SM 1.6-1.7% faster through L2; with 4 edges per lane at 4 CTAs per
+// SM (the WD step now) 1.7% faster through L1 (6.59 -> 6.48 ms).
 #ifndef LB_SSSP_STATUS_CG
-#define LB_SSSP_STATUS_CG 1
+#define LB_SSSP_STATUS_CG 0
 #endif
 // SSSP relax of R loaded edges per lane with deferred atomics
 // (FlushOut::defer == 3): the plain distance check for every item, then
