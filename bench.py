@@ -660,6 +660,8 @@ def main():
                 G.set_options(hp_mode=1 if label == "HP_binned" else 0, ns_mode=1 if label == "NS_binned" else 0)
                 tot = 0.0
                 e_tot = 0
+                b_tot = 0
+                per_q = []
                 exact = True
                 for s in cmp_src:
                     query(kind, s, s_name)   # warm (builds its workspace / loop)
@@ -669,11 +671,20 @@ def main():
                     query(kind, s, s_name)
                     b.record(stream)
                     torch.cuda.synchronize()
-                    tot += a.elapsed_time(b)
-                    e_tot += work[(kind, int(s))][0]
+                    ms = a.elapsed_time(b)
+                    tot += ms
+                    m_r, n_r = work[(kind, int(s))][0], work[(kind, int(s))][1]
+                    e_tot += m_r
+                    b_tot += BYTES[kind][0] * m_r + BYTES[kind][1] * n_r
+                    per_q.append(m_r / (ms / 1e3) / 1e9)
                     exact = exact and G.stats()["status"] == 0 and bool(torch.equal(out, wd_ref[int(s)]))
+                alg = b_tot / (tot / 1e3) / 1e9
+                mem = G.mem_report(s_name)
                 row[label] = {"ms_per_query": tot / len(cmp_src), "gteps": e_tot / (tot / 1e3) / 1e9,
-                              "exact_vs_wd": exact}
+                              "gteps_mean": float(np.mean(per_q)),
+                              "gteps_hmean": float(len(per_q) / sum(1.0 / x for x in per_q)),
+                              "gteps_min": float(min(per_q)), "algorithmic_gbs": alg, "hbm_frac": alg / peak,
+                              "extra_device_bytes": int(mem["extra_total"]), "exact_vs_wd": exact}
             del wd_ref
             G.set_options(hp_mode=0, ns_mode=0)
             row["speedup_wd_vs_bs"] = row["BS"]["ms_per_query"] / row["WD"]["ms_per_query"]
