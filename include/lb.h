@@ -291,9 +291,12 @@ lb_status lb_release_workspaces(lb_graph *g);
  * 4096 edges; NS -- the granule size (MDT from the histogram, or 32 / 256 /
  * 2048) in the paper's form, and the binned form with the histogram MDT or
  * 256 / 2048 x thread bin 8 / 32 / 128; NS_PHYS -- the granule size; BS, EP
- * -- CTAs per SM.  Then, with the fastest of these, WD with small_edges 0
- * (no persistent small-list launch and no conditional node for it), and
- * the eight bitmap placements (bitmap_place).  Fields outside the grid keep their values.
+ * -- CTAs per SM, each timed once.  Then, for WD, small_edges 0 (no
+ * persistent small-list launch and no conditional node for it) against the
+ * fastest grid option, and the eight bitmap placements (bitmap_place) of
+ * each of the three fastest grid options.  Wherever the final choice is
+ * made, the three fastest candidates are timed twice more and ranked by
+ * the sum of their timings.  Fields outside the grid keep their values.
  * On any failure the options in force before the call are restored. */
 lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *srcs, int32_t nsrc, lb_options *best,
                       double *best_ms);

@@ -1115,20 +1115,24 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
         *t = tot;
         return LB_OK;
     };
+    // Every candidate timed once, fastest first (usable ones only).
+    auto time_all = [&](const std::vector<lb_options> &cs, lb_status *err) {
+        std::vector<std::pair<double, int>> t;
+        for (size_t i = 0; i < cs.size() && *err == LB_OK; ++i) {
+            bool ok = false;
+            double tot = 0.0;
+            *err = time_opts(cs[i], &ok, &tot);
+            if (*err == LB_OK && ok) t.push_back({tot, (int)i});
+        }
+        std::sort(t.begin(), t.end());
+        return t;
+    };
     // One timing per candidate, then the three fastest are timed twice more
     // (interleaved) and ranked by the sum of their three timings, so one
     // noisy timing does not pick the options.  Returns the index in cs.
     auto pick = [&](const std::vector<lb_options> &cs, lb_status *err) -> int {
-        std::vector<std::pair<double, int>> t;
-        for (size_t i = 0; i < cs.size(); ++i) {
-            bool ok = false;
-            double tot = 0.0;
-            *err = time_opts(cs[i], &ok, &tot);
-            if (*err != LB_OK) return -1;
-            if (ok) t.push_back({tot, (int)i});
-        }
-        if (t.empty()) return -1;
-        std::sort(t.begin(), t.end());
+        std::vector<std::pair<double, int>> t = time_all(cs, err);
+        if (*err != LB_OK || t.empty()) return -1;
         if (t.size() > 3) t.resize(3);
         for (int rep = 0; rep < 2 && t.size() > 1; ++rep)
             for (auto &c : t) {
@@ -1142,30 +1146,43 @@ lb_status lb_autotune(lb_graph *g, int32_t kind, lb_strategy s, const int32_t *s
         best_t = t[0].first / (t.size() > 1 ? 3.0 : 1.0);
         return t[0].second;
     };
+    // The grid at the caller's bitmap placement; the three fastest options
+    // go on to the placement pass.
+    std::vector<lb_options> top;
     {
         lb_status err = LB_OK;
-        const int i = pick(cands, &err);
+        const std::vector<std::pair<double, int>> t = time_all(cands, &err);
         if (err != LB_OK) return restore(err);
-        if (i >= 0) best_o = cands[(size_t)i];
+        for (size_t k = 0; k < t.size() && k < 3; ++k) top.push_back(cands[(size_t)t[k].second]);
+        if (!t.empty()) {
+            best_t = t[0].first;
+            best_o = top[0];
+        }
     }
-    // then where the bitmap lies, with the fastest options; and for WD
-    // whether the persistent small-list launch is worth its conditional
-    // node (a few microseconds per level on graphs that never run it)
-    if (best_t < 1e300 && s == LB_WD && best_o.small_edges != 0) {
-        std::vector<lb_options> two{best_o, best_o};
+    // For WD, whether the persistent small-list launch is worth its
+    // conditional node (a few microseconds per level on graphs that never
+    // run it), decided on the fastest grid option and applied to all three.
+    if (!top.empty() && s == LB_WD && top[0].small_edges != 0) {
+        std::vector<lb_options> two{top[0], top[0]};
         two[1].small_edges = 0;
         lb_status err = LB_OK;
         const int i = pick(two, &err);
         if (err != LB_OK) return restore(err);
-        if (i >= 0) best_o = two[(size_t)i];
+        if (i == 1)
+            for (lb_options &o : top) o.small_edges = 0;
+        if (i >= 0) best_o = top[0];
     }
-    if (best_t < 1e300) {
+    // Then every bitmap placement of each of the three (the placement and
+    // the grid shape interact: a placement that is slow for one CTA count
+    // can make another win the grid pass).
+    if (!top.empty()) {
         std::vector<lb_options> places;
-        for (int32_t pl = 0; pl < kBitmapPlaces; ++pl) {
-            lb_options o = best_o;
-            o.bitmap_place = pl;
-            places.push_back(o);
-        }
+        for (const lb_options &t : top)
+            for (int32_t pl = 0; pl < kBitmapPlaces; ++pl) {
+                lb_options o = t;
+                o.bitmap_place = pl;
+                places.push_back(o);
+            }
         lb_status err = LB_OK;
         const int i = pick(places, &err);
         if (err != LB_OK) return restore(err);
