@@ -118,8 +118,8 @@ typedef struct lb_options {
                               their own MDT, the histogram MDT of the
                               remaining degrees of that list's entries (the
                               super list uses the graph's MDT); later
-                              sub-lists keep the last one (Sec. III-C: "the
-                              depth of this hierarchy is tunable") */
+                              sub-lists keep the last one (Sec. III-C leaves
+                              the depth of the hierarchy to the user) */
     int32_t small_edges;   /* WD: while the worklist has at most this many
                               edges, levels run inside one persistent launch
                               (one CTA per SM, a grid barrier between levels)
