@@ -708,8 +708,16 @@ def main():
         hb = hb_t.numpy()
         hbu = hb.view(np.uint32)
         src_list = [int(s) for s in srcs]
-        G.bfs(int(srcs[0]), strat)  # warm
-        lb.lb_bfs_batch(G.h, src_list[:2], strat, hb[:2 * n])  # warm (second result buffer, copy stream)
+        # warm both kinds (the comparison above released the workspaces, so
+        # each kind's workspace and device loop are rebuilt here, outside
+        # the timed region), the second result buffer and the copy stream
+        for kind in kinds:
+            if kind == "bfs":
+                G.bfs(src_list[0], strat)
+                lb.lb_bfs_batch(G.h, src_list[:2], strat, hb[:2 * n])
+            else:
+                G.sssp(src_list[0], strat)
+                lb.lb_sssp_batch(G.h, src_list[:2], strat, hbu[:2 * n])
         e_done = sum(work[(kind, s)][0] for kind in kinds for s in src_list)
         t0 = time.perf_counter()
         for kind in kinds:

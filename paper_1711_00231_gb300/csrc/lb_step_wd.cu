@@ -5,7 +5,32 @@
 
 namespace lbk {
 
+// Preferred shared-memory carve-out of the WD step kernels in percent of
+// the largest (-1: the driver's choice).  The rest of the unified L1 /
+// shared memory caches the randomly read visited bitmap (BFS) and
+// distances (SSSP).  25% selects the 64 KB configuration, which holds the
+// resident CTAs' push buffers (BFS: 6 x (9.1 + 1) KB with 96-entry buffers;
+// SSSP: 4 x (12.1 + 1) KB) and leaves 192 KB of L1; the driver's own choice
+// left less.  Measured on R-MAT scale 24: BFS 1.764 -> 1.672 ms, SSSP 6.48
+// -> 6.28 ms per query.
+#ifndef LB_WD_CARVEOUT_BFS
+#define LB_WD_CARVEOUT_BFS 25
+#endif
+#ifndef LB_WD_CARVEOUT_SSSP
+#define LB_WD_CARVEOUT_SSSP 25
+#endif
+
 cudaError_t launch_step_wd(bool sssp, const StepParams &p, int grid, cudaStream_t st) {
+    if (LB_WD_CARVEOUT_BFS >= 0 && !sssp) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_wd<false, kItemsWdBfs>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout, LB_WD_CARVEOUT_BFS);
+        if (e != cudaSuccess) return e;
+    }
+    if (LB_WD_CARVEOUT_SSSP >= 0 && sssp) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_wd<true, kItemsWdSssp>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout, LB_WD_CARVEOUT_SSSP);
+        if (e != cudaSuccess) return e;
+    }
     if (sssp) k_step_wd<true, kItemsWdSssp><<<grid, kBlock, 0, st>>>(p);
     else k_step_wd<false, kItemsWdBfs><<<grid, kBlock, 0, st>>>(p);
     return cudaGetLastError();

@@ -63,7 +63,7 @@ __device__ __forceinline__ uint32_t u4_get(const uint4 &x, int r) {
 // shared-memory footprint decides the L1 carve-out left for the randomly
 // read visited bitmap and distances.
 #ifndef LB_KWB_WD_BFS
-#define LB_KWB_WD_BFS 128
+#define LB_KWB_WD_BFS 96
 #endif
 #ifndef LB_KWB_WD_SSSP
 #define LB_KWB_WD_SSSP 128
