@@ -634,7 +634,7 @@ def main():
         return {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
                 "traffic": None,
                 "traffic_note": "captured at R-MAT scale 22 only (profiles/k_step_wd_traffic_rmat22_ef32.md: BFS "
-                                "0.66x, SSSP 1.71x the algorithmic bytes per query); not scaled, since at scale 24 "
+                                "0.65x, SSSP 1.72x the algorithmic bytes per query); not scaled, since at scale 24 "
                                 "the distance array no longer fits in L2 and traffic does not grow in proportion",
                 "kernel": f"k_step_wd ({kind})", "peak_source": f"{peak_kind} hbm_gbs",
                 "unit_of_work": "one query (all its relax launches + set-up); algorithmic bytes per query "
