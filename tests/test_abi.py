@@ -142,3 +142,15 @@ def test_server_argument_errors_need_no_gpu():
 def test_binding_names_match_header():
     for name in declared_functions():
         assert hasattr(lb, name), f"binding lacks {name}"
+
+
+def test_batch_sources_are_marshalled_as_int32():
+    # the batched calls take any 1-D sequence of vertex ids; the binding
+    # passes it as a contiguous int32 array and refuses what cannot be one
+    a = lb._sources([3, 1, 2])
+    assert a.dtype == np.int32 and a.flags["C_CONTIGUOUS"] and a.tolist() == [3, 1, 2]
+    assert lb._sources([]).size == 0
+    with pytest.raises(ValueError):
+        lb._sources([[0, 1]])
+    with pytest.raises(ValueError):
+        lb._sources([1 << 31])
